@@ -1,0 +1,352 @@
+#!/usr/bin/env python3
+"""Benchmark of the Montgomery multiplication hot path on one GB300 per rank.
+
+Workload (one step): elementwise mont_mul (a b R^-1 mod P) and mont_fma
+((a b R^-1 + c) mod P) over 2^28 uint32 residues per operand, uniform in
+[0, P), for each of the Fourier primes 2013265921, 469762049 and 754974721:
+six kernel launches, 6 x 2^28 modular multiplications.  Each operand is
+1 GiB, far larger than L2, so no L2 flush is needed between steps.
+
+Prints one JSON line (rank 0).  `value` is Gmulmod/s over all ranks (weak
+scaling: each rank runs its own replica of the workload).  `roofline` is
+the dominant kernel's algorithmic bytes per launch over its CUDA-event
+duration, against the measured HBM copy bandwidth.  `cpu_baseline` is the
+CPU oracle timed on the host cores on one full step of the same workload.
+
+--impl reference times the CPU oracle itself on a bounded sample of the
+same workload per step (there is no reference implementation to install:
+the paper publishes no code).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1609_00999_gb300 import synth  # noqa: E402
+
+N_ELEM = 1 << 28
+OPS = ("mont_mul", "mont_fma")
+BYTES_PER_ELEM = {"mont_mul": 12, "mont_fma": 16}
+METRIC = "Gmulmod/s (elementwise mont_mul + mont_fma)"
+UNIT = "Gmulmod/s"
+WORKLOAD = ("elementwise mont_mul + mont_fma over 2^28 uint32 residues per operand, uniform in [0,P), "
+            "P in {2013265921, 469762049, 754974721}")
+KERNEL_SOURCES = ("paper_1609_00999_gb300/csrc/elementwise.cu", "paper_1609_00999_gb300/csrc/mont_arith.cuh")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("gb300", "reference"), default="gb300")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--log2n", type=int, default=28, help="elements per operand (default 2^28)")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def source_digest(paths):
+    h = hashlib.sha256()
+    for pth in paths:
+        with open(os.path.join(ROOT, pth), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel_key, n_elem):
+    """DRAM bytes per launch from the committed ncu summary, scaled to n_elem, or None
+    when the kernel source changed since the counters were taken."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            rec = json.load(f)[kernel_key]
+    except Exception:
+        return None
+    if rec.get("source_digest") != source_digest(KERNEL_SOURCES):
+        return None
+    return rec["dram_bytes_per_launch"] * n_elem / rec["elements_per_launch"]
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+    FIELDS = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id=None):
+        self.bus_id = (bus_id or "").lower()
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 10:
+                    continue
+                rows.append(parts)
+        os.unlink(self.path)
+        if self.bus_id:
+            mine = [r for r in rows if r[1].lower().endswith(self.bus_id[-12:])]
+            rows = mine or rows
+        if rows:
+            idx = rows[0][0]
+            rows = [r for r in rows if r[0] == idx]
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        smax = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        reasons = set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            for name, v in zip(names, r[6:10]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def cpu_oracle_step(arrays, n_sample):
+    """Oracle mont_mul + mont_fma over the first n_sample elements of each prime's operands."""
+    import oracle
+    t0 = time.perf_counter()
+    for p, (a, b, c) in arrays:
+        oracle.mont_mul(p, a[:n_sample], b[:n_sample])
+        oracle.mont_fma(p, a[:n_sample], b[:n_sample], c[:n_sample])
+    return time.perf_counter() - t0
+
+
+def run_reference(args, ws, rank):
+    """CPU oracle on a bounded sample of the same workload, per step."""
+    if rank != 0:
+        return
+    import oracle
+    n_sample = 1 << min(22, args.log2n)
+    arrays = []
+    for i in range(3):
+        p, ops = synth.elementwise_large(i, n=n_sample)
+        arrays.append((p, ops))
+    for _ in range(args.warmup):
+        cpu_oracle_step(arrays, n_sample)
+    t = 0.0
+    for _ in range(args.steps):
+        t += cpu_oracle_step(arrays, n_sample)
+    mulmods = args.steps * 3 * 2 * n_sample
+    value = mulmods / t / 1e9
+    sample = "first 2^%d residues of each operand, 3 primes x {mont_mul, mont_fma}, per step" % (
+        n_sample.bit_length() - 1)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic (seeded PCG64)",
+            "config": {"workload": WORKLOAD, "n_per_operand": 1 << args.log2n,
+                       "sample_per_step": n_sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, ws, rank, local):
+    import torch
+    import paper_1609_00999_gb300 as m
+    from paper_1609_00999_gb300 import build as gbuild
+
+    gbuild.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    n = 1 << args.log2n
+    arrays, dev = [], []
+    for i in range(3):
+        p, (a, b, c) = synth.elementwise_large(i, n=n)
+        arrays.append((p, (a, b, c)))
+        ctx = m.mont_setup(p)
+        tens = [torch.from_numpy(x.view(np.int32)).cuda() for x in (a, b, c)]
+        dev.append((ctx, tens, torch.empty_like(tens[0])))
+    stream = torch.cuda.current_stream()
+
+    def step(events=None):
+        for ctx, (a, b, c), out in dev:
+            for op in OPS:
+                if events is not None:
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                if op == "mont_mul":
+                    m.mont_mul(ctx, a, b, out=out)
+                else:
+                    m.mont_fma(ctx, a, b, c, out=out)
+                if events is not None:
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e1.record(stream)
+                    events[op].append((e0, e1))
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    bus = None
+    try:
+        bus = torch.cuda.get_device_properties(local).pci_bus_id
+    except Exception:
+        pass
+    sampler = ClockSampler(bus)
+    sampler.start()
+    time.sleep(0.3)
+    events = {op: [] for op in OPS}
+    barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step(events)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    elapsed_ms = t0.elapsed_time(t1)
+    if dist is not None:
+        tt = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(tt.item())
+    launches = args.steps * len(dev) * len(OPS)
+    per_op_ms = {op: [e0.elapsed_time(e1) for e0, e1 in events[op]] for op in OPS}
+    mulmods = args.steps * len(dev) * len(OPS) * n * ws
+    value = mulmods / (elapsed_ms / 1e3) / 1e9
+
+    dominant = max(OPS, key=lambda op: sum(per_op_ms[op]))
+    avg_ms = sum(per_op_ms[dominant]) / len(per_op_ms[dominant])
+    alg_bytes = BYTES_PER_ELEM[dominant] * n
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / (avg_ms / 1e3) / 1e9
+    kernel_key = "k_elementwise<%s>" % ("OP_FMA" if dominant == "mont_fma" else "OP_MUL")
+    roofline = {"bound": "hbm", "kernel": kernel_key, "achieved": achieved, "peak": peak,
+                "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": recorded_traffic(kernel_key, n), "algorithmic_bytes": alg_bytes,
+                "avg_launch_ms": avg_ms,
+                "per_op_avg_ms": {op: sum(v) / len(v) for op, v in per_op_ms.items()},
+                "per_op_gbs": {op: BYTES_PER_ELEM[op] * n / (sum(v) / len(v) / 1e3) / 1e9
+                               for op, v in per_op_ms.items()}}
+
+    # End to end: pinned host operands -> device -> kernels -> host results, every step.
+    e2e = None
+    if args.e2e_steps > 0:
+        host = []
+        for p, (a, b, c) in arrays:
+            hin = [torch.from_numpy(x.view(np.int32)).pin_memory() for x in (a, b, c)]
+            hout = [torch.empty(n, dtype=torch.int32, pin_memory=True) for _ in OPS]
+            host.append((hin, hout))
+
+        def e2e_step():
+            for (ctx, (a, b, c), out), (hin, hout) in zip(dev, host):
+                a.copy_(hin[0], non_blocking=True)
+                b.copy_(hin[1], non_blocking=True)
+                c.copy_(hin[2], non_blocking=True)
+                m.mont_mul(ctx, a, b, out=out)
+                hout[0].copy_(out, non_blocking=True)
+                m.mont_fma(ctx, a, b, c, out=out)
+                hout[1].copy_(out, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        w0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        e2e_s = time.perf_counter() - w0
+        if dist is not None:
+            tt = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_s = float(tt.item())
+        e2e = {"value": args.e2e_steps * len(dev) * len(OPS) * n * ws / e2e_s / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": 3 * 3 * 4 * n, "d2h_bytes_per_step": 3 * 2 * 4 * n,
+               "steps": args.e2e_steps,
+               "path": "pinned host -> cudaMemcpyAsync -> C-ABI kernels -> pinned host, one stream"}
+        del host
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        t = cpu_oracle_step(arrays, n)
+        cpu = {"value": 3 * 2 * n / t / 1e9, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": "one full step: 2^%d residues x 3 primes x {mont_mul, mont_fma}" % args.log2n}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded PCG64)",
+                "config": {"workload": WORKLOAD, "n_per_operand": n, "primes": list(synth.PRIMES),
+                           "launches_per_step": len(dev) * len(OPS),
+                           "l2": "operands (1 GiB each) larger than L2; no flush",
+                           "parallelism": "replica per GPU" if ws > 1 else "single GPU"},
+                "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+                "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_gpu(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,92 @@
+/*
+ * mont.h -- C ABI of the GB300 (sm_103a) Montgomery multiplication library.
+ *
+ * Montgomery multiplication of 32-bit residues after L. Meng, "Automatic
+ * Generation of Vectorized Montgomery Algorithm", Sec. 3.1 (Alg. 2, REDC) and
+ * Sec. 3.2 (its data-parallel form), with R = 2^32 and P' = -P^-1 mod R.
+ *
+ * Conventions shared by every entry point:
+ *  - Data pointers are DEVICE pointers (or memory the device can address,
+ *    e.g. pinned host memory) owned by the caller; the library never frees
+ *    them.  Elements are uint32 residues, contiguous, in [0, P).  Inputs
+ *    outside [0, P) give unspecified (but in-bounds, non-faulting) results.
+ *  - Calls are asynchronous on `stream` (0 = the legacy default stream) of
+ *    the current device; they return once the work is queued.
+ *  - Return value: MONT_OK (0) or a negative MONT_E* code.  Argument errors
+ *    are detected on the host before anything is queued; a launch failure
+ *    returns MONT_ECUDA.  No C++ exception crosses this boundary.
+ *  - n == 0 is a no-op returning MONT_OK.
+ *  - Elementwise calls allow out to equal an input (in place); any other
+ *    overlap of an output with an input is rejected with MONT_EINVAL.
+ */
+#ifndef GB300_MONT_H
+#define GB300_MONT_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    MONT_OK = 0,
+    MONT_EINVAL = -1,      /* bad argument (modulus, pointer, size, overlap, flags)   */
+    MONT_ENOMEM = -2,      /* device or host allocation failed                         */
+    MONT_ERANGE = -3,      /* size beyond what the modulus / plan supports             */
+    MONT_ETIMEOUT = -4,    /* a bounded device-side wait gave up                       */
+    MONT_ECUDA = -5,       /* a CUDA runtime call or kernel launch failed              */
+    MONT_EUNSUPPORTED = -6 /* valid request this build does not implement              */
+};
+
+/*
+ * Montgomery context (Sec. 3.1: "P' with R R^-1 - P P' = 1", residues
+ * i-bar = iR mod P).  Plain caller-owned POD; filled by mont_setup and
+ * validated by every call that takes it.
+ *   p        odd modulus, 3 <= p < 2^31 (so 2P < R and the REDC sum fits 32 bits)
+ *   p_prime  P' = -P^-1 mod 2^32
+ *   r_mod_p  R mod P  (the Montgomery form of 1)
+ *   r2_mod_p R^2 mod P (to_mont multiplies by it through REDC)
+ */
+typedef struct mont_ctx {
+    uint32_t p;
+    uint32_t p_prime;
+    uint32_t r_mod_p;
+    uint32_t r2_mod_p;
+} mont_ctx;
+
+/* Host only, no device work.  MONT_EINVAL if p is even, p < 3, p >= 2^31 or out is NULL. */
+int mont_setup(uint32_t p, mont_ctx *out);
+
+/*
+ * out[i] = in[i] R mod P  (Sec. 3.1 residue map), computed as REDC(in[i] * (R^2 mod P)).
+ */
+int to_mont(const mont_ctx *ctx, const uint32_t *in, uint32_t *out, size_t n, cudaStream_t stream);
+
+/* out[i] = in[i] R^-1 mod P, computed as REDC(in[i] * 1). */
+int from_mont(const mont_ctx *ctx, const uint32_t *in, uint32_t *out, size_t n, cudaStream_t stream);
+
+/*
+ * out[i] = REDC(a[i], b[i]) = a[i] b[i] R^-1 mod P, fully reduced to [0, P)
+ * (Alg. 2: T = ab; m = (T mod R) P' mod R; t = (T + mP)/R; one conditional
+ * subtract).  With Montgomery-form operands a = xR, b = yR the result is xyR.
+ */
+int mont_mul(const mont_ctx *ctx, const uint32_t *a, const uint32_t *b, uint32_t *out, size_t n,
+             cudaStream_t stream);
+
+/*
+ * out[i] = (REDC(a[i], b[i]) + c[i]) mod P: a Montgomery multiply followed by
+ * a modular add, which Sec. 3.1 notes is unchanged by the representation.
+ * With a = xR, b = yR, c = zR the result is (xy + z)R mod P.
+ */
+int mont_fma(const mont_ctx *ctx, const uint32_t *a, const uint32_t *b, const uint32_t *c,
+             uint32_t *out, size_t n, cudaStream_t stream);
+
+/* Static description of a return code; never NULL. */
+const char *mont_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,10 @@
+"""GB300-native Montgomery multiplication, NTT and polynomial multiplication.
+
+The computation runs in hand-written sm_103a CUDA kernels behind the C ABI of
+``include/mont.h`` (``libmontgomery.so``); this package is the thin Python
+binding over that ABI, with the same names.  Build the library with
+``paper_1609_00999_gb300.build.build()``.
+"""
+from ._binding import (MONT_ECUDA, MONT_EINVAL, MONT_ENOMEM, MONT_ERANGE, MONT_ETIMEOUT,  # noqa: F401
+                       MONT_EUNSUPPORTED, MONT_OK, MontCtx, MontError, from_mont, lib, mont_fma,
+                       mont_mul, mont_setup, strerror, to_mont)

@@ -1,0 +1,173 @@
+"""ctypes binding over ``libmontgomery.so`` (the C ABI declared in include/mont.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels behind the C ABI.  Tensors are torch CUDA tensors of dtype int32 or
+uint32 holding residues in [0, P); the current torch stream of the tensor's
+device is used unless a stream is given.  There is no CPU path: if the
+library has not been built, every call raises.
+"""
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmontgomery.so")
+
+MONT_OK = 0
+MONT_EINVAL = -1
+MONT_ENOMEM = -2
+MONT_ERANGE = -3
+MONT_ETIMEOUT = -4
+MONT_ECUDA = -5
+MONT_EUNSUPPORTED = -6
+
+_vp = ctypes.c_void_p
+_sz = ctypes.c_size_t
+
+
+class MontError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        super().__init__("%s: %s (%d)" % (what, strerror(code), code))
+
+
+class MontCtx(ctypes.Structure):
+    """Mirror of ``mont_ctx``: p, P' = -P^-1 mod 2^32, R mod P, R^2 mod P."""
+    _fields_ = [("p", ctypes.c_uint32), ("p_prime", ctypes.c_uint32),
+                ("r_mod_p", ctypes.c_uint32), ("r2_mod_p", ctypes.c_uint32)]
+
+    def __repr__(self):
+        return "MontCtx(p=%d, p_prime=%d, r_mod_p=%d, r2_mod_p=%d)" % (
+            self.p, self.p_prime, self.r_mod_p, self.r2_mod_p)
+
+
+_lib = None
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libmontgomery.so is not built; run paper_1609_00999_gb300.build.build() "
+                               "(or __graft_entry__.build()) first")
+        L = ctypes.CDLL(LIB_PATH)
+        _declare(L)
+        _lib = L
+    return _lib
+
+
+def _declare(L):
+    ctxp = ctypes.POINTER(MontCtx)
+    L.mont_setup.argtypes = [ctypes.c_uint32, ctxp]
+    L.mont_strerror.argtypes = [ctypes.c_int]
+    L.mont_strerror.restype = ctypes.c_char_p
+    L.to_mont.argtypes = [ctxp, _vp, _vp, _sz, _vp]
+    L.from_mont.argtypes = [ctxp, _vp, _vp, _sz, _vp]
+    L.mont_mul.argtypes = [ctxp, _vp, _vp, _vp, _sz, _vp]
+    L.mont_fma.argtypes = [ctxp, _vp, _vp, _vp, _vp, _sz, _vp]
+    for name in ("mont_setup", "to_mont", "from_mont", "mont_mul", "mont_fma"):
+        getattr(L, name).restype = ctypes.c_int
+    try:
+        _declare_ntt(L)
+    except AttributeError:
+        pass
+
+
+def _declare_ntt(L):
+    pass
+
+
+def strerror(code):
+    try:
+        return lib().mont_strerror(code).decode()
+    except RuntimeError:
+        return "error %d" % code
+
+
+def _check(rc, what):
+    if rc != MONT_OK:
+        raise MontError(rc, what)
+
+
+_U32_DTYPES = (torch.int32,) + ((torch.uint32,) if hasattr(torch, "uint32") else ())
+
+
+def _dev_ptr(t, name):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s must be a torch tensor" % name)
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if t.dtype not in _U32_DTYPES:
+        raise TypeError("%s must be int32 or uint32 (got %s)" % (name, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return t.data_ptr()
+
+
+def _stream_handle(stream, device):
+    if stream is None:
+        return torch.cuda.current_stream(device).cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def mont_setup(p):
+    """Montgomery context for modulus p (host only)."""
+    ctx = MontCtx()
+    _check(lib().mont_setup(int(p), ctypes.byref(ctx)), "mont_setup(%r)" % (p,))
+    return ctx
+
+
+def _ctx(ctx):
+    return ctx if isinstance(ctx, MontCtx) else mont_setup(ctx)
+
+
+def _out_like(x, out):
+    if out is None:
+        return torch.empty_like(x)
+    if out.numel() != x.numel():
+        raise ValueError("out has %d elements, expected %d" % (out.numel(), x.numel()))
+    return out
+
+
+def to_mont(ctx, x, out=None, stream=None):
+    """out = x R mod P (elementwise)."""
+    ctx = _ctx(ctx)
+    out = _out_like(x, out)
+    _check(lib().to_mont(ctypes.byref(ctx), _dev_ptr(x, "x"), _dev_ptr(out, "out"), x.numel(),
+                         _stream_handle(stream, x.device)), "to_mont")
+    return out
+
+
+def from_mont(ctx, x, out=None, stream=None):
+    """out = x R^-1 mod P (elementwise)."""
+    ctx = _ctx(ctx)
+    out = _out_like(x, out)
+    _check(lib().from_mont(ctypes.byref(ctx), _dev_ptr(x, "x"), _dev_ptr(out, "out"), x.numel(),
+                           _stream_handle(stream, x.device)), "from_mont")
+    return out
+
+
+def mont_mul(ctx, a, b, out=None, stream=None):
+    """out = REDC(a, b) = a b R^-1 mod P (elementwise, Alg. 2)."""
+    ctx = _ctx(ctx)
+    if a.numel() != b.numel():
+        raise ValueError("a and b differ in size")
+    out = _out_like(a, out)
+    _check(lib().mont_mul(ctypes.byref(ctx), _dev_ptr(a, "a"), _dev_ptr(b, "b"), _dev_ptr(out, "out"),
+                          a.numel(), _stream_handle(stream, a.device)), "mont_mul")
+    return out
+
+
+def mont_fma(ctx, a, b, c, out=None, stream=None):
+    """out = (REDC(a, b) + c) mod P (elementwise)."""
+    ctx = _ctx(ctx)
+    if not (a.numel() == b.numel() == c.numel()):
+        raise ValueError("a, b and c differ in size")
+    out = _out_like(a, out)
+    _check(lib().mont_fma(ctypes.byref(ctx), _dev_ptr(a, "a"), _dev_ptr(b, "b"), _dev_ptr(c, "c"),
+                          _dev_ptr(out, "out"), a.numel(), _stream_handle(stream, a.device)), "mont_fma")
+    return out

@@ -15,7 +15,9 @@ libraries of Sec. 1 and 5):
   three Fourier primes; Poisson arrivals (exponential gaps) for request
   streams.
 """
+import concurrent.futures as _cf
 import math
+import os
 
 import numpy as np
 
@@ -38,9 +40,28 @@ def rng(*key):
     return np.random.Generator(np.random.PCG64(np.random.SeedSequence(list(key))))
 
 
+_CHUNK = 1 << 22
+
+
+def _fill_chunk(args):
+    out, lo, hi, p, key = args
+    out[lo:hi] = rng(*key, lo // _CHUNK).integers(0, p, size=hi - lo, dtype=np.uint32)
+
+
 def residues(n, p, *key):
-    """n residues uniform in [0, p) as uint32."""
-    return rng(*key).integers(0, p, size=n, dtype=np.uint32)
+    """n residues uniform in [0, p) as uint32.
+
+    Drawn in chunks of 2^22, chunk i from its own stream (key..., i), so the
+    values do not depend on how many threads fill the array."""
+    out = np.empty(n, dtype=np.uint32)
+    jobs = [(out, lo, min(n, lo + _CHUNK), p, key) for lo in range(0, n, _CHUNK)]
+    if len(jobs) <= 1:
+        for j in jobs:
+            _fill_chunk(j)
+    else:
+        with _cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4, 32)) as ex:
+            list(ex.map(_fill_chunk, jobs))
+    return out
 
 
 def loguniform_lengths(count, lo, hi, *key):
