@@ -83,6 +83,55 @@ int mont_mul(const mont_ctx *ctx, const uint32_t *a, const uint32_t *b, uint32_t
 int mont_fma(const mont_ctx *ctx, const uint32_t *a, const uint32_t *b, const uint32_t *c,
              uint32_t *out, size_t n, cudaStream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Number-theoretic transform and polynomial multiplication.
+ *
+ * The modular FFT over Z_P that the paper's generated libraries compute
+ * (Sec. 1 and 5; the paper does not restate it): X_k = sum_j x_j w^(jk) mod P
+ * for N = 2^log2n, w = g^((P-1)/N), g the smallest primitive root of P.
+ * The butterflies multiply by Montgomery-form twiddles with REDC (Alg. 2);
+ * data stay in plain (non-Montgomery) form in [0, P).
+ * ------------------------------------------------------------------------ */
+
+/* Opaque plan: prime, size and the library-owned, device-resident twiddle
+ * tables of the device current at creation.  Create and destroy on the host;
+ * use only with that device current. */
+typedef struct ntt_plan ntt_plan;
+
+/* Flag for ntt_fwd: leave the output in bit-reversed order.
+ * Flag for ntt_inv: the input is in bit-reversed order. */
+#define NTT_BITREV 1
+
+/* p prime, 3 <= p < 2^31, 2^log2n divides p - 1, log2n <= 24.  Builds (or
+ * reuses) the twiddle tables with cudaMalloc/cudaMemcpy (synchronous; do not
+ * call during stream capture).  MONT_EINVAL for a bad prime or NULL out,
+ * MONT_ERANGE for an unsupported size, MONT_ENOMEM / MONT_ECUDA on failure. */
+int ntt_plan_create(uint32_t p, uint32_t log2n, ntt_plan **out);
+void ntt_plan_destroy(ntt_plan *plan);
+
+/* In-place forward transform of `batch` contiguous rows of N residues
+ * ([batch][N] row-major).  Natural order in; natural order out unless
+ * flags has NTT_BITREV.  N <= 2^14 (else MONT_EUNSUPPORTED). */
+int ntt_fwd(const ntt_plan *plan, uint32_t *data, size_t batch, int flags, cudaStream_t stream);
+
+/* In-place inverse transform including the factor N^-1: ntt_inv(ntt_fwd(x)) = x.
+ * Natural-order input unless flags has NTT_BITREV; natural-order output. */
+int ntt_inv(const ntt_plan *plan, uint32_t *data, size_t batch, int flags, cudaStream_t stream);
+
+/* c = a * b mod p (polynomials, coefficient 0 first), c has la + lb - 1
+ * coefficients; a, b in [0, p).  Computed as forward NTTs of both operands
+ * zero-padded to N = 2^ceil(log2(la + lb - 1)), a pointwise REDC product and
+ * an inverse NTT, fused per product.  la, lb >= 1 (else MONT_EINVAL); c may
+ * not overlap a or b.  The twiddle tables are built on first use for
+ * (device, p, N): make the first call outside stream capture. */
+int polymul(uint32_t p, const uint32_t *a, size_t la, const uint32_t *b, size_t lb, uint32_t *c,
+            cudaStream_t stream);
+
+/* `count` independent products of the same shape: a is [count][la], b is
+ * [count][lb], c is [count][la + lb - 1], all row-major and contiguous. */
+int polymul_many(uint32_t p, const uint32_t *a, size_t la, const uint32_t *b, size_t lb, uint32_t *c,
+                 size_t count, cudaStream_t stream);
+
 /* Static description of a return code; never NULL. */
 const char *mont_strerror(int code);
 

@@ -6,5 +6,6 @@ binding over that ABI, with the same names.  Build the library with
 ``paper_1609_00999_gb300.build.build()``.
 """
 from ._binding import (MONT_ECUDA, MONT_EINVAL, MONT_ENOMEM, MONT_ERANGE, MONT_ETIMEOUT,  # noqa: F401
-                       MONT_EUNSUPPORTED, MONT_OK, MontCtx, MontError, from_mont, lib, mont_fma,
-                       mont_mul, mont_setup, strerror, to_mont)
+                       MONT_EUNSUPPORTED, MONT_OK, NTT_BITREV, MontCtx, MontError, NttPlan, from_mont,
+                       lib, mont_fma, mont_mul, mont_setup, ntt_fwd, ntt_inv, ntt_plan_create, polymul,
+                       polymul_many, strerror, to_mont)

@@ -69,14 +69,21 @@ def _declare(L):
     L.mont_fma.argtypes = [ctxp, _vp, _vp, _vp, _vp, _sz, _vp]
     for name in ("mont_setup", "to_mont", "from_mont", "mont_mul", "mont_fma"):
         getattr(L, name).restype = ctypes.c_int
-    try:
-        _declare_ntt(L)
-    except AttributeError:
-        pass
+    _declare_ntt(L)
 
 
 def _declare_ntt(L):
-    pass
+    L.ntt_plan_create.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(_vp)]
+    L.ntt_plan_create.restype = ctypes.c_int
+    L.ntt_plan_destroy.argtypes = [_vp]
+    L.ntt_plan_destroy.restype = None
+    for name in ("ntt_fwd", "ntt_inv"):
+        getattr(L, name).argtypes = [_vp, _vp, _sz, ctypes.c_int, _vp]
+        getattr(L, name).restype = ctypes.c_int
+    L.polymul.argtypes = [ctypes.c_uint32, _vp, _sz, _vp, _sz, _vp, _vp]
+    L.polymul.restype = ctypes.c_int
+    L.polymul_many.argtypes = [ctypes.c_uint32, _vp, _sz, _vp, _sz, _vp, _sz, _vp]
+    L.polymul_many.restype = ctypes.c_int
 
 
 def strerror(code):
@@ -170,4 +177,79 @@ def mont_fma(ctx, a, b, c, out=None, stream=None):
     out = _out_like(a, out)
     _check(lib().mont_fma(ctypes.byref(ctx), _dev_ptr(a, "a"), _dev_ptr(b, "b"), _dev_ptr(c, "c"),
                           _dev_ptr(out, "out"), a.numel(), _stream_handle(stream, a.device)), "mont_fma")
+    return out
+
+
+NTT_BITREV = 1
+
+
+class NttPlan:
+    """Owner of an ``ntt_plan *`` (prime p, size 2^log2n, resident twiddles)."""
+
+    def __init__(self, p, log2n):
+        h = _vp()
+        _check(lib().ntt_plan_create(int(p), int(log2n), ctypes.byref(h)), "ntt_plan_create(%r, %r)" % (p, log2n))
+        self._h = h
+        self.p = int(p)
+        self.log2n = int(log2n)
+        self.n = 1 << self.log2n
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.ntt_plan_destroy(h)
+            self._h = None
+
+
+def ntt_plan_create(p, log2n):
+    return NttPlan(p, log2n)
+
+
+def _ntt(name, plan, data, flags, stream):
+    if data.numel() % plan.n:
+        raise ValueError("data size %d is not a multiple of N = %d" % (data.numel(), plan.n))
+    _check(getattr(lib(), name)(plan.handle, _dev_ptr(data, "data"), data.numel() // plan.n, int(flags),
+                                _stream_handle(stream, data.device)), name)
+    return data
+
+
+def ntt_fwd(plan, data, flags=0, stream=None):
+    """In-place forward NTT of each row of N residues (natural order unless NTT_BITREV)."""
+    return _ntt("ntt_fwd", plan, data, flags, stream)
+
+
+def ntt_inv(plan, data, flags=0, stream=None):
+    """In-place inverse NTT (with N^-1) of each row; input bit-reversed if NTT_BITREV."""
+    return _ntt("ntt_inv", plan, data, flags, stream)
+
+
+def polymul(p, a, b, out=None, stream=None):
+    """c = a * b mod p for 1-D coefficient tensors; c has len(a) + len(b) - 1 entries."""
+    lc = a.numel() + b.numel() - 1
+    if out is None:
+        out = torch.empty(max(lc, 0), dtype=a.dtype, device=a.device)
+    elif out.numel() != lc:
+        raise ValueError("out must have %d elements" % lc)
+    _check(lib().polymul(int(p), _dev_ptr(a, "a"), a.numel(), _dev_ptr(b, "b"), b.numel(), _dev_ptr(out, "out"),
+                         _stream_handle(stream, a.device)), "polymul")
+    return out
+
+
+def polymul_many(p, a, b, out=None, stream=None):
+    """Row-wise products of a [count][la] and b [count][lb] -> [count][la + lb - 1]."""
+    if a.dim() != 2 or b.dim() != 2 or a.shape[0] != b.shape[0]:
+        raise ValueError("a and b must be [count][la] and [count][lb]")
+    count, la = a.shape
+    lb = b.shape[1]
+    lc = la + lb - 1
+    if out is None:
+        out = torch.empty((count, lc), dtype=a.dtype, device=a.device)
+    elif out.numel() != count * lc:
+        raise ValueError("out must have %d elements" % (count * lc))
+    _check(lib().polymul_many(int(p), _dev_ptr(a, "a"), la, _dev_ptr(b, "b"), lb, _dev_ptr(out, "out"), count,
+                              _stream_handle(stream, a.device)), "polymul_many")
     return out
