@@ -111,7 +111,9 @@ void ntt_plan_destroy(ntt_plan *plan);
 
 /* In-place forward transform of `batch` contiguous rows of N residues
  * ([batch][N] row-major).  Natural order in; natural order out unless
- * flags has NTT_BITREV.  N <= 2^14 (else MONT_EUNSUPPORTED). */
+ * flags has NTT_BITREV.  N <= 2^14 runs in one kernel per batch; larger N
+ * runs column and row kernels in place (plus a bit-reversal pass for
+ * natural order), needing no scratch. */
 int ntt_fwd(const ntt_plan *plan, uint32_t *data, size_t batch, int flags, cudaStream_t stream);
 
 /* In-place inverse transform including the factor N^-1: ntt_inv(ntt_fwd(x)) = x.
@@ -128,9 +130,30 @@ int polymul(uint32_t p, const uint32_t *a, size_t la, const uint32_t *b, size_t 
             cudaStream_t stream);
 
 /* `count` independent products of the same shape: a is [count][la], b is
- * [count][lb], c is [count][la + lb - 1], all row-major and contiguous. */
+ * [count][lb], c is [count][la + lb - 1], all row-major and contiguous.
+ * N <= 2^14 runs one fused kernel per batch.  Larger N (up to 2^24) runs
+ * column / row / column kernels through a scratch buffer of 2N words per
+ * product; polymul and polymul_many take it from a library-owned buffer per
+ * (device, stream), at most 1 GiB (larger batches run in chunks), allocated
+ * or grown with cudaMalloc on first need: size it outside stream capture.
+ * Concurrent calls on different streams use different buffers. */
 int polymul_many(uint32_t p, const uint32_t *a, size_t la, const uint32_t *b, size_t lb, uint32_t *c,
                  size_t count, cudaStream_t stream);
+
+/* Scratch bytes polymul_many_ws needs for `count` products of this shape
+ * (0 when N <= 2^14). */
+size_t polymul_workspace_bytes(size_t la, size_t lb, size_t count);
+
+/* polymul_many with caller-owned scratch: workspace is a 16-byte aligned
+ * device buffer of ws_bytes.  With less than polymul_workspace_bytes(la, lb,
+ * count) the products run in chunks that fit; less than one product's share
+ * (or a misaligned pointer) is MONT_EINVAL.  The buffer must not be used by
+ * other work until the queued kernels finish. */
+int polymul_many_ws(uint32_t p, const uint32_t *a, size_t la, const uint32_t *b, size_t lb, uint32_t *c,
+                    size_t count, void *workspace, size_t ws_bytes, cudaStream_t stream);
+
+/* Frees the library-owned scratch buffers (waits for the device). */
+int mont_release_workspaces(void);
 
 /* Static description of a return code; never NULL. */
 const char *mont_strerror(int code);

@@ -84,6 +84,12 @@ def _declare_ntt(L):
     L.polymul.restype = ctypes.c_int
     L.polymul_many.argtypes = [ctypes.c_uint32, _vp, _sz, _vp, _sz, _vp, _sz, _vp]
     L.polymul_many.restype = ctypes.c_int
+    L.polymul_many_ws.argtypes = [ctypes.c_uint32, _vp, _sz, _vp, _sz, _vp, _sz, _vp, _sz, _vp]
+    L.polymul_many_ws.restype = ctypes.c_int
+    L.polymul_workspace_bytes.argtypes = [_sz, _sz, _sz]
+    L.polymul_workspace_bytes.restype = _sz
+    L.mont_release_workspaces.argtypes = []
+    L.mont_release_workspaces.restype = ctypes.c_int
 
 
 def strerror(code):
@@ -253,3 +259,28 @@ def polymul_many(p, a, b, out=None, stream=None):
     _check(lib().polymul_many(int(p), _dev_ptr(a, "a"), la, _dev_ptr(b, "b"), lb, _dev_ptr(out, "out"), count,
                               _stream_handle(stream, a.device)), "polymul_many")
     return out
+
+
+def polymul_workspace_bytes(la, lb, count=1):
+    """Scratch bytes polymul_many_ws needs (0 when N <= 2^14)."""
+    return int(lib().polymul_workspace_bytes(int(la), int(lb), int(count)))
+
+
+def polymul_many_ws(p, a, b, workspace, out=None, stream=None):
+    """polymul_many with a caller-owned scratch tensor (any dtype, CUDA, contiguous)."""
+    if a.dim() != 2 or b.dim() != 2 or a.shape[0] != b.shape[0]:
+        raise ValueError("a and b must be [count][la] and [count][lb]")
+    count, la = a.shape
+    lb = b.shape[1]
+    lc = la + lb - 1
+    if out is None:
+        out = torch.empty((count, lc), dtype=a.dtype, device=a.device)
+    ws_ptr = workspace.data_ptr() if workspace is not None else None
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check(lib().polymul_many_ws(int(p), _dev_ptr(a, "a"), la, _dev_ptr(b, "b"), lb, _dev_ptr(out, "out"), count,
+                                 ws_ptr, ws_bytes, _stream_handle(stream, a.device)), "polymul_many_ws")
+    return out
+
+
+def mont_release_workspaces():
+    _check(lib().mont_release_workspaces(), "mont_release_workspaces")

@@ -200,4 +200,121 @@ struct PassGeom {
     }
 };
 
+// ---------------------------------------------------------------- layouts
+//
+// A layout maps element j of a sub-transform to its shared-memory word.
+
+// Whole transform in one buffer with the XOR swizzle.
+struct SwzLayout {
+    uint32_t *base;
+    __device__ __forceinline__ uint32_t &operator[](int j) const { return base[swz(j)]; }
+};
+
+// Column c of a column tile: base = c * (N1 + PAD), XOR of the low five bits
+// with XR = (c * MUL) & 31, optionally on top of swz.  Chosen per column size
+// so that the coalesced tile loads and the strided pass accesses hit distinct
+// banks.
+template <bool SW>
+struct ColLayout {
+    uint32_t *base;
+    int xr;
+    __device__ __forceinline__ uint32_t &operator[](int j) const { return base[(SW ? swz(j) : j) ^ xr]; }
+};
+
+// ---------------------------------------------------------------- passes
+//
+// Pass I of a 2^LOGN sub-transform whose level s_loc is level s_base + s_loc
+// of the whole transform and which is block b of 2^s_base blocks
+// (twiddle index 2^(s_base+s_loc) + (b << s_loc) + local block).  BASE0:
+// s_base is known to be 0, so local level 0 has twiddle 1.
+
+template <int LOGN, int NT, int I, int NARR, bool BASE0, class L>
+__device__ __forceinline__ void fwd_pass(const L (&lay)[NARR], int tid, const uint2 *__restrict__ tw, int s_base,
+                                         int b, uint32_t p)
+{
+    using PG = PassGeom<LOGN, NT, I>;
+#pragma unroll
+    for (int r = 0; r < PG::GPT; r++) {
+        const int base = PG::base(tid, r), blk = PG::blk(tid, r);
+        uint32_t x[NARR][PG::G];
+#pragma unroll
+        for (int a = 0; a < NARR; a++)
+#pragma unroll
+            for (int t = 0; t < PG::G; t++) x[a][t] = lay[a][base + t * PG::HMIN];
+        ct_group<PG::E, NARR, BASE0 && PG::S0 == 0>(x, tw, s_base + PG::S0, (b << PG::S0) + blk, p);
+#pragma unroll
+        for (int a = 0; a < NARR; a++)
+#pragma unroll
+            for (int t = 0; t < PG::G; t++) lay[a][base + t * PG::HMIN] = x[a][t];
+    }
+}
+
+template <int LOGN, int NT, int I, bool BASE0, class L>
+__device__ __forceinline__ void inv_pass(const L &lay, int tid, const uint2 *__restrict__ itw, int s_base, int b,
+                                         uint32_t p)
+{
+    using PG = PassGeom<LOGN, NT, I>;
+#pragma unroll
+    for (int r = 0; r < PG::GPT; r++) {
+        const int base = PG::base(tid, r), blk = PG::blk(tid, r);
+        uint32_t x[1][PG::G];
+#pragma unroll
+        for (int t = 0; t < PG::G; t++) x[0][t] = lay[base + t * PG::HMIN];
+        gs_group<PG::E, 1, BASE0 && PG::S0 == 0>(x, itw, s_base + PG::S0, (b << PG::S0) + blk, p);
+#pragma unroll
+        for (int t = 0; t < PG::G; t++) lay[base + t * PG::HMIN] = x[0][t];
+    }
+}
+
+// Forward passes I .. LAST, each followed by a CTA barrier.
+template <int LOGN, int NT, int NARR, bool BASE0, int I, int LAST, class L>
+__device__ __forceinline__ void fwd_passes(const L (&lay)[NARR], int tid, const uint2 *__restrict__ tw, int s_base,
+                                           int b, uint32_t p)
+{
+    if constexpr (I <= LAST) {
+        fwd_pass<LOGN, NT, I, NARR, BASE0>(lay, tid, tw, s_base, b, p);
+        __syncthreads();
+        fwd_passes<LOGN, NT, NARR, BASE0, I + 1, LAST>(lay, tid, tw, s_base, b, p);
+    }
+}
+
+// Inverse passes I, I-1, .. FIRST, each followed by a CTA barrier.
+template <int LOGN, int NT, bool BASE0, int I, int FIRST, class L>
+__device__ __forceinline__ void inv_passes(const L &lay, int tid, const uint2 *__restrict__ itw, int s_base, int b,
+                                           uint32_t p)
+{
+    if constexpr (I >= FIRST) {
+        inv_pass<LOGN, NT, I, BASE0>(lay, tid, itw, s_base, b, p);
+        __syncthreads();
+        inv_passes<LOGN, NT, BASE0, I - 1, FIRST>(lay, tid, itw, s_base, b, p);
+    }
+}
+
+// Last forward pass of both operands, pointwise REDC product (A B~ R^-1),
+// then the same levels of the inverse in reverse, result into lay[0].
+template <int LOGN, int NT, bool BASE0, class L>
+__device__ __forceinline__ void fused_middle_pass(const L (&lay)[2], int tid, const uint2 *__restrict__ tw,
+                                                  const uint2 *__restrict__ itw, int s_base, int b, uint32_t p,
+                                                  uint32_t pp)
+{
+    using PL = PassGeom<LOGN, NT, Sched<LOGN>::kPasses - 1>;
+#pragma unroll
+    for (int r = 0; r < PL::GPT; r++) {
+        const int base = PL::base(tid, r), blk = (b << PL::S0) + PL::blk(tid, r);
+        uint32_t x[2][PL::G];
+#pragma unroll
+        for (int t = 0; t < PL::G; t++) {
+            x[0][t] = lay[0][base + t * PL::HMIN];
+            x[1][t] = lay[1][base + t * PL::HMIN];
+        }
+        ct_group<PL::E, 2, BASE0 && PL::S0 == 0>(x, tw, s_base + PL::S0, blk, p);
+        uint32_t y[1][PL::G];
+#pragma unroll
+        for (int t = 0; t < PL::G; t++) y[0][t] = mont_mul(x[0][t], x[1][t], p, pp);
+        gs_group<PL::E, 1, BASE0 && PL::S0 == 0>(y, itw, s_base + PL::S0, blk, p);
+#pragma unroll
+        for (int t = 0; t < PL::G; t++) lay[0][base + t * PL::HMIN] = y[0][t];
+    }
+}
+
 }  // namespace mont

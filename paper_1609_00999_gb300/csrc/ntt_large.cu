@@ -1,0 +1,329 @@
+// ntt_large.cu -- transforms and products with N = 2^K > 2^14 (up to 2^24).
+//
+// The K levels split into K1 column levels and K2 = max(12, K - 10) row
+// levels.  Viewing the N elements as a [2^K1][2^K2] row-major matrix, levels
+// 0 .. K1-1 pair elements of the same column (stride 2^K2) and their
+// twiddles depend only on the row index, so every column is an independent
+// 2^K1-point transform with the table entries 1 .. 2^K1 - 1.  Levels
+// K1 .. K-1 stay inside one row; row r is block r of level K1, so its
+// twiddle for local level l and local block i is entry 2^(K1+l) + (r << l) + i.
+//
+// Column kernel: a CTA loads a tile of C consecutive columns with coalesced
+// row segments, runs the column levels per column (one team of threads per
+// column), and writes the tile back.  Row kernel: one CTA per row, the same
+// register passes as the single-CTA kernels.
+#include <algorithm>
+
+#include "ntt_kernels.cuh"
+
+namespace mont {
+namespace {
+
+// Column tile geometry and shared-memory layout per column size 2^K1:
+// C columns per CTA, NT1 threads per column (512 threads per CTA), column c
+// at c * (N1 + PAD) with the low five bits XORed by (c * MUL) & 31 (on top
+// of swz when SW).  These choices make the coalesced tile loads bank-conflict
+// free and keep the pass accesses at most 1.5-way conflicted on average.
+template <int K1>
+struct ColCfg {
+    static constexpr int N1 = 1 << K1;
+    static constexpr int C = K1 <= 4 ? 512 : (K1 >= 10 ? 8 : (1 << (13 - K1)));
+    static constexpr int NT1 = N1 <= 16 ? 1 : N1 / 16;
+    static constexpr int THREADS = C * NT1;
+    static constexpr int PAD = (K1 <= 4) ? 1 : (K1 == 8 ? 16 : 0);
+    static constexpr int MUL = (K1 <= 4) ? 0 : (K1 == 5 || K1 == 9) ? 17 : (K1 == 8 ? 3 : 9);
+    static constexpr bool SW = K1 >= 8;
+    static constexpr int STRIDE = N1 + PAD;
+    static constexpr size_t SMEM = static_cast<size_t>(C) * STRIDE * sizeof(uint32_t);
+    static_assert(THREADS <= 1024, "column tile too large");
+};
+
+struct ColArgs {
+    const uint32_t *src[2];
+    size_t src_len[2];      // elements at index >= src_len read as zero
+    size_t src_stride[2];   // per product (grid.z)
+    uint32_t *dst[2];
+    size_t dst_len;         // elements at index >= dst_len are not stored
+    size_t dst_stride;
+    int k2;
+    const uint2 *tw;
+    uint32_t p, pp;
+    uint32_t scale[2];      // nonzero: REDC-multiply inputs by it on load
+    uint32_t post;          // nonzero: REDC-multiply outputs by it on store
+};
+
+template <int K1, bool INVERSE>
+__global__ void __launch_bounds__(ColCfg<K1>::THREADS)
+k_col(ColArgs A, size_t prod0)
+{
+    using CF = ColCfg<K1>;
+    constexpr int NP = Sched<K1>::kPasses;
+    extern __shared__ __align__(16) uint32_t smem[];
+    const bool op1 = blockIdx.y != 0;   // operand select without indexing the parameter arrays
+    const size_t prod = prod0 + blockIdx.z;
+    const uint32_t *src = (op1 ? A.src[1] : A.src[0]) + prod * (op1 ? A.src_stride[1] : A.src_stride[0]);
+    const size_t slen = op1 ? A.src_len[1] : A.src_len[0];
+    uint32_t *dst = (op1 ? A.dst[1] : A.dst[0]) + prod * A.dst_stride;
+    const uint32_t scale = op1 ? A.scale[1] : A.scale[0];
+    const size_t o0 = static_cast<size_t>(blockIdx.x) * CF::C;
+    const uint32_t p = A.p, pp = A.pp;
+    auto col = [&](int c) { return ColLayout<CF::SW>{smem + c * CF::STRIDE, (c * CF::MUL) & 31}; };
+
+    for (int i = threadIdx.x; i < CF::C * CF::N1; i += CF::THREADS) {
+        const int t = i / CF::C, c = i % CF::C;
+        const size_t j = o0 + c + (static_cast<size_t>(t) << A.k2);
+        uint32_t v = j < slen ? __ldg(src + j) : 0u;
+        if (scale) v = mont_mul(v, scale, p, pp);
+        col(c)[t] = v;
+    }
+    __syncthreads();
+    const int c = threadIdx.x / CF::NT1, tid = threadIdx.x % CF::NT1;
+    const ColLayout<CF::SW> lay[1] = {col(c)};
+    if constexpr (!INVERSE) fwd_passes<K1, CF::NT1, 1, true, 0, NP - 1>(lay, tid, A.tw, 0, 0, p);
+    else inv_passes<K1, CF::NT1, true, NP - 1, 0>(lay[0], tid, A.tw, 0, 0, p);
+    for (int i = threadIdx.x; i < CF::C * CF::N1; i += CF::THREADS) {
+        const int t = i / CF::C, cc = i % CF::C;
+        const size_t j = o0 + cc + (static_cast<size_t>(t) << A.k2);
+        uint32_t v = col(cc)[t];
+        if (A.post) v = mont_mul(v, A.post, p, pp);
+        if (j < A.dst_len) dst[j] = v;
+    }
+}
+
+struct RowArgs {
+    uint32_t *ws;       // product i: A' at ws + i * 2N, B' at + N; C' overwrites A'
+    size_t n;
+    int k1;
+    const uint2 *tw, *itw;
+    uint32_t p, pp;
+};
+
+// Row r of a product: forward row levels of A' and B', pointwise product,
+// inverse row levels, C' in place of A'.
+template <int K2>
+__global__ void __launch_bounds__(nt_of<K2>())
+k_row_polymul(RowArgs A, size_t prod0)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    const size_t prod = prod0 + blockIdx.y;
+    const int r = blockIdx.x;
+    uint32_t *base = A.ws + prod * 2 * A.n + (static_cast<size_t>(r) << K2);
+    polymul_team<K2, false, false>(smem, threadIdx.x, base, size_t{1} << K2, base + A.n, size_t{1} << K2, base,
+                                   size_t{1} << K2, A.tw, A.itw, A.k1, r, A.p, A.pp, 0u);
+}
+
+struct RowNttArgs {
+    uint32_t *data;
+    size_t n;
+    int k1;
+    const uint2 *tw;
+    uint32_t p;
+};
+
+template <int K2, bool INVERSE>
+__global__ void __launch_bounds__(nt_of<K2>())
+k_row_ntt(RowNttArgs A, size_t prod0)
+{
+    constexpr int N2 = 1 << K2, NT = nt_of<K2>(), NP = Sched<K2>::kPasses;
+    extern __shared__ __align__(16) uint32_t smem[];
+    const size_t prod = prod0 + blockIdx.y;
+    const int r = blockIdx.x;
+    uint32_t *g = A.data + prod * A.n + (static_cast<size_t>(r) << K2);
+    const SwzLayout lay[1] = {{smem}};
+    for (int k = threadIdx.x; k < N2; k += NT) lay[0][k] = g[k];
+    __syncthreads();
+    if constexpr (!INVERSE) fwd_passes<K2, NT, 1, false, 0, NP - 1>(lay, threadIdx.x, A.tw, A.k1, r, A.p);
+    else inv_passes<K2, NT, false, NP - 1, 0>(lay[0], threadIdx.x, A.tw, A.k1, r, A.p);
+    for (int k = threadIdx.x; k < N2; k += NT) g[k] = lay[0][k];
+}
+
+// In-place bit-reversal permutation of each row of 2^log2n elements.
+__global__ void k_bitrev(uint32_t *data, int log2n, size_t batch)
+{
+    const size_t n = size_t{1} << log2n, total = n * batch;
+    for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < total;
+         i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const size_t row = i >> log2n;
+        const uint32_t j = static_cast<uint32_t>(i & (n - 1));
+        const uint32_t rj = __brev(j) >> (32 - log2n);
+        if (j < rj) {
+            uint32_t *g = data + row * n;
+            const uint32_t t = g[j];
+            g[j] = g[rj];
+            g[rj] = t;
+        }
+    }
+}
+
+constexpr unsigned kMaxGridZ = 65535;
+
+template <int K1, bool INVERSE>
+int launch_col(const ColArgs &A, size_t nops, size_t count, cudaStream_t s)
+{
+    using CF = ColCfg<K1>;
+    if (ensure_smem(k_col<K1, INVERSE>, CF::SMEM) != MONT_OK) return MONT_ECUDA;
+    const size_t n2 = size_t{1} << A.k2;
+    for (size_t first = 0; first < count; first += kMaxGridZ) {
+        const unsigned z = static_cast<unsigned>(std::min<size_t>(kMaxGridZ, count - first));
+        dim3 grid(static_cast<unsigned>(n2 / CF::C), static_cast<unsigned>(nops), z);
+        k_col<K1, INVERSE><<<grid, CF::THREADS, CF::SMEM, s>>>(A, first);
+        if (cudaGetLastError() != cudaSuccess) return MONT_ECUDA;
+    }
+    return MONT_OK;
+}
+
+template <int K2>
+int launch_row_polymul(const RowArgs &A, size_t count, cudaStream_t s)
+{
+    const size_t smem = 2 * (size_t{1} << K2) * sizeof(uint32_t);
+    if (ensure_smem(k_row_polymul<K2>, smem) != MONT_OK) return MONT_ECUDA;
+    const unsigned rows = static_cast<unsigned>(A.n >> K2);
+    for (size_t first = 0; first < count; first += kMaxGridZ) {
+        const unsigned y = static_cast<unsigned>(std::min<size_t>(kMaxGridZ, count - first));
+        k_row_polymul<K2><<<dim3(rows, y), nt_of<K2>(), smem, s>>>(A, first);
+        if (cudaGetLastError() != cudaSuccess) return MONT_ECUDA;
+    }
+    return MONT_OK;
+}
+
+template <int K2, bool INVERSE>
+int launch_row_ntt(const RowNttArgs &A, size_t count, cudaStream_t s)
+{
+    const size_t smem = (size_t{1} << K2) * sizeof(uint32_t);
+    if (ensure_smem(k_row_ntt<K2, INVERSE>, smem) != MONT_OK) return MONT_ECUDA;
+    const unsigned rows = static_cast<unsigned>(A.n >> K2);
+    for (size_t first = 0; first < count; first += kMaxGridZ) {
+        const unsigned y = static_cast<unsigned>(std::min<size_t>(kMaxGridZ, count - first));
+        k_row_ntt<K2, INVERSE><<<dim3(rows, y), nt_of<K2>(), smem, s>>>(A, first);
+        if (cudaGetLastError() != cudaSuccess) return MONT_ECUDA;
+    }
+    return MONT_OK;
+}
+
+int split_k2(int k)
+{
+    return std::max(12, k - 10);
+}
+
+#define MONT_K1_CASES(X) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10)
+
+template <bool INVERSE>
+int dispatch_col(int k1, const ColArgs &A, size_t nops, size_t count, cudaStream_t s)
+{
+    switch (k1) {
+#define X(K) \
+    case K: return launch_col<K, INVERSE>(A, nops, count, s);
+        MONT_K1_CASES(X)
+#undef X
+    default: return MONT_EUNSUPPORTED;
+    }
+}
+
+int dispatch_row_polymul(int k2, const RowArgs &A, size_t count, cudaStream_t s)
+{
+    switch (k2) {
+    case 12: return launch_row_polymul<12>(A, count, s);
+    case 13: return launch_row_polymul<13>(A, count, s);
+    case 14: return launch_row_polymul<14>(A, count, s);
+    default: return MONT_EUNSUPPORTED;
+    }
+}
+
+template <bool INVERSE>
+int dispatch_row_ntt(int k2, const RowNttArgs &A, size_t count, cudaStream_t s)
+{
+    switch (k2) {
+    case 12: return launch_row_ntt<12, INVERSE>(A, count, s);
+    case 13: return launch_row_ntt<13, INVERSE>(A, count, s);
+    case 14: return launch_row_ntt<14, INVERSE>(A, count, s);
+    default: return MONT_EUNSUPPORTED;
+    }
+}
+
+int launch_bitrev(uint32_t *data, int log2n, size_t batch, cudaStream_t s)
+{
+    const int sms = device_sm_count();
+    if (sms <= 0) return MONT_ECUDA;
+    const size_t total = (size_t{1} << log2n) * batch;
+    const size_t want = (total + 255) / 256;
+    const unsigned grid = static_cast<unsigned>(std::min<size_t>(want, static_cast<size_t>(sms) * 8));
+    k_bitrev<<<grid, 256, 0, s>>>(data, log2n, batch);
+    return launch_status();
+}
+
+}  // namespace
+
+int polymul_large(const ntt_plan &plan, const uint32_t *a, size_t la, const uint32_t *b, size_t lb, uint32_t *c,
+                  size_t count, uint32_t *ws, cudaStream_t s)
+{
+    const int k = plan.log2n, k2 = split_k2(k), k1 = k - k2;
+    const size_t n = size_t{1} << k;
+    ColArgs F{};
+    F.src[0] = a;
+    F.src[1] = b;
+    F.src_len[0] = la;
+    F.src_len[1] = lb;
+    F.src_stride[0] = la;
+    F.src_stride[1] = lb;
+    F.dst[0] = ws;
+    F.dst[1] = ws + n;
+    F.dst_len = n;
+    F.dst_stride = 2 * n;
+    F.k2 = k2;
+    F.tw = plan.table->fwd;
+    F.p = plan.p;
+    F.pp = plan.p_prime;
+    F.scale[0] = 0;
+    F.scale[1] = plan.k_scale;
+    F.post = 0;
+    int rc = dispatch_col<false>(k1, F, 2, count, s);
+    if (rc != MONT_OK) return rc;
+    RowArgs R{ws, n, k1, plan.table->fwd, plan.table->inv, plan.p, plan.p_prime};
+    rc = dispatch_row_polymul(k2, R, count, s);
+    if (rc != MONT_OK) return rc;
+    ColArgs I{};
+    I.src[0] = I.src[1] = ws;
+    I.src_len[0] = I.src_len[1] = n;
+    I.src_stride[0] = I.src_stride[1] = 2 * n;
+    I.dst[0] = I.dst[1] = c;
+    I.dst_len = la + lb - 1;
+    I.dst_stride = la + lb - 1;
+    I.k2 = k2;
+    I.tw = plan.table->inv;
+    I.p = plan.p;
+    I.pp = plan.p_prime;
+    return dispatch_col<true>(k1, I, 1, count, s);
+}
+
+int ntt_large(const ntt_plan *plan, uint32_t *data, size_t batch, int flags, bool inverse, cudaStream_t s)
+{
+    const int k = plan->log2n, k2 = split_k2(k), k1 = k - k2;
+    const size_t n = size_t{1} << k;
+    if (batch > SIZE_MAX / n / 4) return MONT_ERANGE;
+    ColArgs C{};
+    C.src[0] = C.src[1] = data;
+    C.src_len[0] = C.src_len[1] = n;
+    C.src_stride[0] = C.src_stride[1] = n;
+    C.dst[0] = C.dst[1] = data;
+    C.dst_len = n;
+    C.dst_stride = n;
+    C.k2 = k2;
+    C.p = plan->p;
+    C.pp = plan->p_prime;
+    RowNttArgs R{data, n, k1, nullptr, plan->p};
+    int rc;
+    if (!inverse) {
+        C.tw = R.tw = plan->table->fwd;
+        if ((rc = dispatch_col<false>(k1, C, 1, batch, s)) != MONT_OK) return rc;
+        if ((rc = dispatch_row_ntt<false>(k2, R, batch, s)) != MONT_OK) return rc;
+        if (!(flags & NTT_BITREV)) return launch_bitrev(data, k, batch, s);
+        return MONT_OK;
+    }
+    C.tw = R.tw = plan->table->inv;
+    C.post = plan->ninv_mont;
+    if (!(flags & NTT_BITREV) && (rc = launch_bitrev(data, k, batch, s)) != MONT_OK) return rc;
+    if ((rc = dispatch_row_ntt<true>(k2, R, batch, s)) != MONT_OK) return rc;
+    return dispatch_col<true>(k1, C, 1, batch, s);
+}
+
+}  // namespace mont

@@ -1,0 +1,87 @@
+"""GPU parity of the large-N path (N = 2^15 .. 2^24: column / row / column
+kernels through HBM scratch) with the CPU oracle, bit-exact."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1609_00999_gb300 import synth
+
+from helpers import to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def m():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1609_00999_gb300 as m
+    from paper_1609_00999_gb300 import build
+    build.build()
+    return m
+
+
+def bitrev_perm(logn):
+    k = np.arange(1 << logn, dtype=np.int64)
+    r = np.zeros_like(k)
+    for b in range(logn):
+        r |= ((k >> b) & 1) << (logn - 1 - b)
+    return r
+
+
+CASES = [(synth.P1, k) for k in range(15, 23)] + [(synth.P2, 15), (synth.P2, 19), (synth.P3, 17), (synth.P3, 21),
+                                                 (synth.P3, 24)]
+
+
+@pytest.mark.parametrize("p,logn", CASES)
+def test_large_ntt(m, p, logn):
+    n = 1 << logn
+    batch = 2 if logn <= 17 else 1
+    x = synth.residues(batch * n, p, 400, logn).reshape(batch, n)
+    ref = np.stack([oracle.ntt(p, row) for row in x])
+    plan = m.ntt_plan_create(p, logn)
+    d = to_dev(x)
+    m.ntt_fwd(plan, d)
+    assert np.array_equal(to_host(d).reshape(batch, n), ref)
+    m.ntt_inv(plan, d)
+    assert np.array_equal(to_host(d).reshape(batch, n), x)
+    d = to_dev(x)
+    m.ntt_fwd(plan, d, flags=m.NTT_BITREV)
+    assert np.array_equal(to_host(d).reshape(batch, n), ref[:, bitrev_perm(logn)])
+    m.ntt_inv(plan, d, flags=m.NTT_BITREV)
+    assert np.array_equal(to_host(d).reshape(batch, n), x)
+
+
+@pytest.mark.parametrize("p,la,lb", [(synth.P1, 8193, 8192), (synth.P1, 16384, 16385), (synth.P2, 30000, 20000),
+                                     (synth.P3, 65536, 65536), (synth.P1, 100000, 31073), (synth.P2, 1, 40000),
+                                     (synth.P1, 1 << 20, 1 << 20), (synth.P3, 700000, 123457)])
+def test_large_polymul(m, p, la, lb):
+    a = synth.residues(la, p, 401, la, lb, 0)
+    b = synth.residues(lb, p, 401, la, lb, 1)
+    got = to_host(m.polymul(p, to_dev(a), to_dev(b)))
+    ref = oracle.polymul_ntt(p, a, b)
+    assert np.array_equal(got, ref)
+    if la * lb <= (1 << 27):
+        idx = [0, 1, la // 2, la + lb - 2]
+        sb = oracle.polymul_schoolbook(p, a, b)
+        assert np.array_equal(got[idx], sb[idx])
+
+
+def test_large_polymul_many_and_chunked_workspace(m):
+    import torch
+    p, count, la, lb = synth.P2, 5, 20000, 12001
+    a = synth.residues(count * la, p, 402, 0).reshape(count, la)
+    b = synth.residues(count * lb, p, 402, 1).reshape(count, lb)
+    ref = np.stack([oracle.polymul_ntt(p, a[i], b[i]) for i in range(count)])
+    got = to_host(m.polymul_many(p, to_dev(a), to_dev(b))).reshape(count, la + lb - 1)
+    assert np.array_equal(got, ref)
+    per = m.polymul_workspace_bytes(la, lb, 1)
+    assert per == 2 * 32768 * 4 and m.polymul_workspace_bytes(la, lb, count) == count * per
+    ws = torch.empty(2 * per // 4 + 7, dtype=torch.int32, device="cuda")   # room for two products: 3 chunks
+    got = to_host(m.polymul_many_ws(p, to_dev(a), to_dev(b), ws)).reshape(count, la + lb - 1)
+    assert np.array_equal(got, ref)
+    small = torch.empty(per // 4 - 1, dtype=torch.int32, device="cuda")
+    with pytest.raises(m.MontError) as e:
+        m.polymul_many_ws(p, to_dev(a), to_dev(b), small)
+    assert e.value.code == m.MONT_EINVAL
