@@ -152,6 +152,29 @@ size_t polymul_workspace_bytes(size_t la, size_t lb, size_t count);
 int polymul_many_ws(uint32_t p, const uint32_t *a, size_t la, const uint32_t *b, size_t lb, uint32_t *c,
                     size_t count, void *workspace, size_t ws_bytes, cudaStream_t stream);
 
+/*
+ * polymul without any allocation.  (No counterpart in the paper: this is a
+ * service to callers of this library that cannot call cudaMalloc -- code being
+ * recorded into a CUDA graph, code inside a framework whose allocator owns the
+ * device memory, or latency-critical paths that cannot take cudaMalloc's
+ * implicit device synchronisation.)
+ *
+ * Same result as polymul(plan's prime, a, la, b, lb, c, stream).  The
+ * twiddle tables come from `plan` (created beforehand with ntt_plan_create,
+ * on the current device, for a size 2^k >= la + lb - 1 of the same prime:
+ * larger plans serve smaller products).  Products with N > 2^14 use a fixed
+ * 2 MiB scratch array in the library's device memory instead of allocating:
+ * la + lb - 1 must be <= 2^18 (else MONT_ERANGE; also MONT_ERANGE if the
+ * plan's tables are too short).  Calls no cudaMalloc/cudaFree.  The first
+ * call on each device looks up the array's device address
+ * (cudaGetSymbolAddress): make that first call before any stream capture.
+ * Every call on a device shares the one array, so calls whose kernels
+ * overlap on the GPU (e.g. on different streams) race and must be ordered by
+ * the caller; no state carries over from one call to the next.
+ */
+int polymul_noalloc(const ntt_plan *plan, const uint32_t *a, size_t la, const uint32_t *b, size_t lb,
+                    uint32_t *c, cudaStream_t stream);
+
 /* Frees the library-owned scratch buffers (waits for the device). */
 int mont_release_workspaces(void);
 

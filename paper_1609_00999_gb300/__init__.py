@@ -9,4 +9,4 @@ from ._binding import (MONT_ECUDA, MONT_EINVAL, MONT_ENOMEM, MONT_ERANGE, MONT_E
                        MONT_EUNSUPPORTED, MONT_OK, NTT_BITREV, MontCtx, MontError, NttPlan, from_mont,
                        lib, mont_fma, mont_mul, mont_setup, ntt_fwd, ntt_inv, ntt_plan_create, polymul,
                        polymul_many, strerror, to_mont)
-from ._binding import mont_release_workspaces, polymul_many_ws, polymul_workspace_bytes  # noqa: F401
+from ._binding import mont_release_workspaces, polymul_many_ws, polymul_noalloc, polymul_workspace_bytes  # noqa: F401

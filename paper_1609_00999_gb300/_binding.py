@@ -88,6 +88,8 @@ def _declare_ntt(L):
     L.polymul_many_ws.restype = ctypes.c_int
     L.polymul_workspace_bytes.argtypes = [_sz, _sz, _sz]
     L.polymul_workspace_bytes.restype = _sz
+    L.polymul_noalloc.argtypes = [_vp, _vp, _sz, _vp, _sz, _vp, _vp]
+    L.polymul_noalloc.restype = ctypes.c_int
     L.mont_release_workspaces.argtypes = []
     L.mont_release_workspaces.restype = ctypes.c_int
 
@@ -284,3 +286,18 @@ def polymul_many_ws(p, a, b, workspace, out=None, stream=None):
 
 def mont_release_workspaces():
     _check(lib().mont_release_workspaces(), "mont_release_workspaces")
+
+
+def polymul_noalloc(plan, a, b, out=None, stream=None):
+    """polymul through the entry point that allocates nothing: twiddles from
+    `plan` (same prime, 2^plan.log2n >= len(a) + len(b) - 1), scratch from the
+    library's fixed device array (len(a) + len(b) - 1 <= 2^18).  `out` must be
+    given by callers that cannot let torch allocate."""
+    lc = a.numel() + b.numel() - 1
+    if out is None:
+        out = torch.empty(max(lc, 0), dtype=a.dtype, device=a.device)
+    elif out.numel() != lc:
+        raise ValueError("out must have %d elements" % lc)
+    _check(lib().polymul_noalloc(plan.handle, _dev_ptr(a, "a"), a.numel(), _dev_ptr(b, "b"), b.numel(),
+                                 _dev_ptr(out, "out"), _stream_handle(stream, a.device)), "polymul_noalloc")
+    return out
