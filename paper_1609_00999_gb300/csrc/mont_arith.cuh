@@ -2,14 +2,15 @@
 //
 // Montgomery reduction after Meng, Sec. 3.1 (Alg. 2, REDC).  On sm_103a one
 // thread is one SIMD lane of the paper's Sec. 3.2, so the 64-bit product T
-// arrives directly as its two halves (mul.lo / mul.hi) and no lane gather is
-// needed:
+// arrives in one register pair (its mul.lo / mul.hi halves) and no lane
+// gather is needed:
 //
-//   T = a b             -> (lo, hi) = (mul.lo(a, b), mul.hi(a, b))
-//   m = (T mod R) P'    -> mul.lo(lo, P')        the "short product" (Sec. 3.1/3.2)
-//   t = (T + m P) / R   -> hi + mul.hi(m, P) + carry, where
-//                          lo + mul.lo(m, P) == 0 (mod R), so the low words
-//                          carry 1 exactly when lo != 0
+//   T = a b             -> mul.wide.u32: both 32-bit halves of the product
+//   m = (T mod R) P'    -> mul.lo(lo(T), P')     the "short product" (Sec. 3.1/3.2)
+//   t = (T + m P) / R   -> mad.wide.u32 m, P, T and keep the high word: the
+//                          64-bit sum is exact (T + mP < 2RP < 2^64) and its
+//                          low word is 0, so the carry out of the low words
+//                          is folded into the one multiply-add
 //   t >= P ? t - P : t  -> min(t, t - P) as unsigned (t - P wraps above t when t < P)
 //
 // Requirements (Alg. 2): 0 <= a b < R P.  With P < 2^31 this holds whenever
@@ -28,11 +29,9 @@ __device__ __forceinline__ uint32_t csub(uint32_t t, uint32_t p)
 // REDC of T = a b without the final subtract: returns t in [0, 2P).
 __device__ __forceinline__ uint32_t redc_lazy(uint32_t a, uint32_t b, uint32_t p, uint32_t p_prime)
 {
-    const uint32_t lo = a * b;
-    const uint32_t hi = __umulhi(a, b);
-    const uint32_t m = lo * p_prime;
-    const uint32_t mh = __umulhi(m, p);
-    return hi + mh + (lo != 0u ? 1u : 0u);
+    const uint64_t T = static_cast<uint64_t>(a) * b;
+    const uint32_t m = static_cast<uint32_t>(T) * p_prime;
+    return static_cast<uint32_t>((static_cast<uint64_t>(m) * p + T) >> 32);
 }
 
 // Full REDC (Alg. 2): a b R^-1 mod P in [0, P).

@@ -38,7 +38,7 @@ __device__ __forceinline__ int brev(int k)
 }
 
 template <int LOGN>
-__global__ void __launch_bounds__(teams_of<LOGN>() * nt_of<LOGN>())
+__global__ void __launch_bounds__(teams_of<LOGN>() * nt_of<LOGN>(), min_ctas_of<LOGN>())
 k_polymul(PolyArgs A)
 {
     constexpr int NT = nt_of<LOGN>();
@@ -57,7 +57,7 @@ k_polymul(PolyArgs A)
 struct NttArgs {
     uint32_t *data;
     size_t batch;
-    const uint2 *tw;
+    const uint32_t *tw;
     uint32_t p, pp, ninv_mont;
     int bitrev;
 };
@@ -77,7 +77,7 @@ k_ntt_fwd(NttArgs A)
     const SwzLayout lay[1] = {{smem + static_cast<size_t>(team) * N}};
     for (int k = tid; k < N; k += NT) lay[0][k] = valid ? g[k] : 0u;
     __syncthreads();
-    fwd_passes<LOGN, NT, 1, true, 0, NP - 1>(lay, tid, A.tw, 0, 0, A.p);
+    fwd_passes<LOGN, NT, 1, true, 0, NP - 1>(lay, tid, A.tw, 0, 0, Mod{A.p, A.pp});
     if (valid)
         for (int k = tid; k < N; k += NT) g[k] = lay[0][A.bitrev ? k : brev<LOGN>(k)];
 }
@@ -97,7 +97,7 @@ k_ntt_inv(NttArgs A)
     const SwzLayout lay = {smem + static_cast<size_t>(team) * N};
     for (int k = tid; k < N; k += NT) lay[A.bitrev ? k : brev<LOGN>(k)] = valid ? g[k] : 0u;
     __syncthreads();
-    inv_passes<LOGN, NT, true, NP - 1, 0>(lay, tid, A.tw, 0, 0, A.p);
+    inv_passes<LOGN, NT, true, NP - 1, 0>(lay, tid, A.tw, 0, 0, Mod{A.p, A.pp});
     if (valid)
         for (int k = tid; k < N; k += NT) g[k] = mont_mul(lay[k], A.ninv_mont, A.p, A.pp);
 }

@@ -13,8 +13,8 @@ struct TwTable {
     int device = 0;
     uint32_t p = 0, p_prime = 0, g = 0;
     int log2max = 0;
-    uint2 *fwd = nullptr;   // device, 2^log2max pairs, forward twiddles
-    uint2 *inv = nullptr;   // device, inverse twiddles
+    uint32_t *fwd = nullptr;   // device, 2^log2max forward twiddles (Montgomery form)
+    uint32_t *inv = nullptr;   // device, inverse twiddles
 };
 
 uint32_t host_primitive_root(uint32_t p);

@@ -23,11 +23,20 @@ constexpr int teams_of()
     return nt_of<LOGN>() >= 256 ? 1 : 256 / nt_of<LOGN>();
 }
 
+// CTAs per SM the register budget is sized for: three 256-thread CTAs
+// (at most 85 registers per thread) for the fused products up to 2^12;
+// one CTA for the 512- and 1024-thread transforms.
+template <int LOGN>
+constexpr int min_ctas_of()
+{
+    return teams_of<LOGN>() * nt_of<LOGN>() <= 256 ? 3 : 1;
+}
+
 struct PolyArgs {
     const uint32_t *a, *b;
     uint32_t *c;
     size_t la, lb, lc, count;
-    const uint2 *tw, *itw;
+    const uint32_t *tw, *itw;
     uint32_t p, pp, k_scale;
 };
 
@@ -49,14 +58,15 @@ int ensure_smem(K kernel, size_t bytes)
 // the whole transform (s_base = 0, b_idx = 0 for a complete product).
 // Reads of a and b (lengths la, lb, zero beyond) all happen before the first
 // barrier, so gc may alias ga (in-place row passes).  Every thread of the CTA
-// must call it (it contains __syncthreads).
+// must call it (it contains __syncthreads).  la, lb, lc <= 2^LOGN.
 template <int LOGN, bool BASE0, bool SCALE_B>
 __device__ __forceinline__ void polymul_team(uint32_t *sm, int tid, const uint32_t *ga, size_t la,
                                              const uint32_t *gb, size_t lb, uint32_t *gc, size_t lc,
-                                             const uint2 *__restrict__ tw, const uint2 *__restrict__ itw, int s_base,
+                                             const uint32_t *__restrict__ tw, const uint32_t *__restrict__ itw, int s_base,
                                              int b_idx, uint32_t p, uint32_t pp, uint32_t k_scale)
 {
     constexpr int N = 1 << LOGN, NT = nt_of<LOGN>(), NP = Sched<LOGN>::kPasses;
+    const Mod md{p, pp};
     if constexpr (LOGN == 0) {
         if (lc > 0) {
             const uint32_t bb = SCALE_B ? mont_mul(gb[0], k_scale, p, pp) : gb[0];
@@ -65,53 +75,68 @@ __device__ __forceinline__ void polymul_team(uint32_t *sm, int tid, const uint32
     } else {
         const SwzLayout lay[2] = {{sm}, {sm + N}};
         using P0 = PassGeom<LOGN, NT, 0>;
+        const int la32 = static_cast<int>(la), lb32 = static_cast<int>(lb), lc32 = static_cast<int>(lc);
+        if constexpr (NP == 1) {
 #pragma unroll
-        for (int r = 0; r < P0::GPT; r++) {
-            const int base = P0::base(tid, r);
-            uint32_t x[2][P0::G];
+            for (int r = 0; r < P0::GPT; r++) {
+                const int base = P0::base(tid, r);
+                uint32_t x[2][P0::G];
 #pragma unroll
-            for (int t = 0; t < P0::G; t++) {
-                const size_t j = static_cast<size_t>(base + t * P0::HMIN);
-                x[0][t] = j < la ? __ldg(ga + j) : 0u;
-                const uint32_t bj = j < lb ? __ldg(gb + j) : 0u;
-                x[1][t] = SCALE_B ? mont_mul(bj, k_scale, p, pp) : bj;
-            }
-            ct_group<P0::E, 2, BASE0>(x, tw, s_base, b_idx, p);
-            if constexpr (NP == 1) {
+                for (int t = 0; t < P0::G; t++) {
+                    const int j = base + t * P0::HMIN;
+                    x[0][t] = j < la32 ? __ldg(ga + j) : 0u;
+                    const uint32_t bj = j < lb32 ? __ldg(gb + j) : 0u;
+                    x[1][t] = SCALE_B ? mont_mul(bj, k_scale, p, pp) : bj;
+                }
+                ct_group<P0::E, 2, BASE0>(x, tw, s_base, b_idx, md);
                 uint32_t y[1][P0::G];
 #pragma unroll
                 for (int t = 0; t < P0::G; t++) y[0][t] = mont_mul(x[0][t], x[1][t], p, pp);
-                gs_group<P0::E, 1, BASE0>(y, itw, s_base, b_idx, p);
+                gs_group<P0::E, 1, BASE0>(y, itw, s_base, b_idx, md);
 #pragma unroll
                 for (int t = 0; t < P0::G; t++) {
-                    const size_t j = static_cast<size_t>(base + t * P0::HMIN);
-                    if (j < lc) gc[j] = y[0][t];
+                    const int j = base + t * P0::HMIN;
+                    if (j < lc32) gc[j] = y[0][t];
                 }
-            } else {
+            }
+        } else {
 #pragma unroll
-                for (int t = 0; t < P0::G; t++) {
-                    lay[0][base + t * P0::HMIN] = x[0][t];
-                    lay[1][base + t * P0::HMIN] = x[1][t];
+            for (int a = 0; a < 2; a++) {
+                const uint32_t *g = a ? gb : ga;
+                const int len = a ? lb32 : la32;
+#pragma unroll
+                for (int r = 0; r < P0::GPT; r++) {
+                    const int base = P0::base(tid, r);
+                    uint32_t x[1][P0::G];
+#pragma unroll
+                    for (int t = 0; t < P0::G; t++) {
+                        const int j = base + t * P0::HMIN;
+                        const uint32_t v = j < len ? __ldg(g + j) : 0u;
+                        x[0][t] = (SCALE_B && a) ? mont_mul(v, k_scale, p, pp) : v;
+                    }
+                    ct_group<P0::E, 1, BASE0>(x, tw, s_base, b_idx, md);
+#pragma unroll
+                    for (int t = 0; t < P0::G; t++) lay[a][base + t * P0::HMIN] = x[0][t];
                 }
             }
         }
         if constexpr (NP > 1) {
             __syncthreads();
-            fwd_passes<LOGN, NT, 2, BASE0, 1, NP - 2>(lay, tid, tw, s_base, b_idx, p);
-            fused_middle_pass<LOGN, NT, BASE0>(lay, tid, tw, itw, s_base, b_idx, p, pp);
+            fwd_passes<LOGN, NT, 2, BASE0, 1, NP - 2>(lay, tid, tw, s_base, b_idx, md);
+            fused_middle_pass<LOGN, NT, BASE0>(lay, tid, tw, itw, s_base, b_idx, md);
             __syncthreads();
-            inv_passes<LOGN, NT, BASE0, NP - 2, 1>(lay[0], tid, itw, s_base, b_idx, p);
+            inv_passes<LOGN, NT, BASE0, NP - 2, 1>(lay[0], tid, itw, s_base, b_idx, md);
 #pragma unroll
             for (int r = 0; r < P0::GPT; r++) {
                 const int base = P0::base(tid, r);
                 uint32_t y[1][P0::G];
 #pragma unroll
                 for (int t = 0; t < P0::G; t++) y[0][t] = lay[0][base + t * P0::HMIN];
-                gs_group<P0::E, 1, BASE0>(y, itw, s_base, b_idx, p);
+                gs_group<P0::E, 1, BASE0>(y, itw, s_base, b_idx, md);
 #pragma unroll
                 for (int t = 0; t < P0::G; t++) {
-                    const size_t j = static_cast<size_t>(base + t * P0::HMIN);
-                    if (j < lc) gc[j] = y[0][t];
+                    const int j = base + t * P0::HMIN;
+                    if (j < lc32) gc[j] = y[0][t];
                 }
             }
         }

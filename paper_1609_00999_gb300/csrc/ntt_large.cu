@@ -46,7 +46,7 @@ struct ColArgs {
     size_t dst_len;         // elements at index >= dst_len are not stored
     size_t dst_stride;
     int k2;
-    const uint2 *tw;
+    const uint32_t *tw;
     uint32_t p, pp;
     uint32_t scale[2];      // nonzero: REDC-multiply inputs by it on load
     uint32_t post;          // nonzero: REDC-multiply outputs by it on store
@@ -79,8 +79,8 @@ k_col(ColArgs A, size_t prod0)
     __syncthreads();
     const int c = threadIdx.x / CF::NT1, tid = threadIdx.x % CF::NT1;
     const ColLayout<CF::SW> lay[1] = {col(c)};
-    if constexpr (!INVERSE) fwd_passes<K1, CF::NT1, 1, true, 0, NP - 1>(lay, tid, A.tw, 0, 0, p);
-    else inv_passes<K1, CF::NT1, true, NP - 1, 0>(lay[0], tid, A.tw, 0, 0, p);
+    if constexpr (!INVERSE) fwd_passes<K1, CF::NT1, 1, true, 0, NP - 1>(lay, tid, A.tw, 0, 0, Mod{p, pp});
+    else inv_passes<K1, CF::NT1, true, NP - 1, 0>(lay[0], tid, A.tw, 0, 0, Mod{p, pp});
     for (int i = threadIdx.x; i < CF::C * CF::N1; i += CF::THREADS) {
         const int t = i / CF::C, cc = i % CF::C;
         const size_t j = o0 + cc + (static_cast<size_t>(t) << A.k2);
@@ -94,14 +94,14 @@ struct RowArgs {
     uint32_t *ws;       // product i: A' at ws + i * 2N, B' at + N; C' overwrites A'
     size_t n;
     int k1;
-    const uint2 *tw, *itw;
+    const uint32_t *tw, *itw;
     uint32_t p, pp;
 };
 
 // Row r of a product: forward row levels of A' and B', pointwise product,
 // inverse row levels, C' in place of A'.
 template <int K2>
-__global__ void __launch_bounds__(nt_of<K2>())
+__global__ void __launch_bounds__(nt_of<K2>(), min_ctas_of<K2>())
 k_row_polymul(RowArgs A, size_t prod0)
 {
     extern __shared__ __align__(16) uint32_t smem[];
@@ -116,8 +116,8 @@ struct RowNttArgs {
     uint32_t *data;
     size_t n;
     int k1;
-    const uint2 *tw;
-    uint32_t p;
+    const uint32_t *tw;
+    uint32_t p, pp;
 };
 
 template <int K2, bool INVERSE>
@@ -132,8 +132,8 @@ k_row_ntt(RowNttArgs A, size_t prod0)
     const SwzLayout lay[1] = {{smem}};
     for (int k = threadIdx.x; k < N2; k += NT) lay[0][k] = g[k];
     __syncthreads();
-    if constexpr (!INVERSE) fwd_passes<K2, NT, 1, false, 0, NP - 1>(lay, threadIdx.x, A.tw, A.k1, r, A.p);
-    else inv_passes<K2, NT, false, NP - 1, 0>(lay[0], threadIdx.x, A.tw, A.k1, r, A.p);
+    if constexpr (!INVERSE) fwd_passes<K2, NT, 1, false, 0, NP - 1>(lay, threadIdx.x, A.tw, A.k1, r, Mod{A.p, A.pp});
+    else inv_passes<K2, NT, false, NP - 1, 0>(lay[0], threadIdx.x, A.tw, A.k1, r, Mod{A.p, A.pp});
     for (int k = threadIdx.x; k < N2; k += NT) g[k] = lay[0][k];
 }
 
@@ -310,7 +310,7 @@ int ntt_large(const ntt_plan *plan, uint32_t *data, size_t batch, int flags, boo
     C.k2 = k2;
     C.p = plan->p;
     C.pp = plan->p_prime;
-    RowNttArgs R{data, n, k1, nullptr, plan->p};
+    RowNttArgs R{data, n, k1, nullptr, plan->p, plan->p_prime};
     int rc;
     if (!inverse) {
         C.tw = R.tw = plan->table->fwd;

@@ -3,7 +3,7 @@
 // Table layout (see ntt_core.cuh): entry 2^s + i, s = 0 .. K-1, i < 2^s,
 // holds r = w_(2^(s+1))^bitrev_s(i) (forward) or its inverse, with
 // w_(2^(s+1)) = g^((P-1)/2^(s+1)) and g the smallest primitive root of P.
-// Each entry is the pair (rR mod P, (rR mod P) P' mod 2^32).  The table does
+// Each entry is rR mod P (Montgomery form).  The table does
 // not depend on the transform size, so one table of 2^K entries serves every
 // N <= 2^K; a larger request builds a larger table (older ones stay valid
 // for plans that hold them until the library is unloaded).
@@ -62,9 +62,9 @@ uint32_t bitrev(uint32_t i, int bits)
     return r;
 }
 
-void fill_table(std::vector<uint2> &t, uint32_t p, uint32_t pp, uint32_t g, int log2max, bool inverse)
+void fill_table(std::vector<uint32_t> &t, uint32_t p, uint32_t g, int log2max, bool inverse)
 {
-    t.assign(size_t{1} << log2max, make_uint2(0, 0));
+    t.assign(size_t{1} << log2max, 0u);
     std::vector<uint32_t> pw;
     for (int s = 0; s < log2max; s++) {
         const uint32_t m = 1u << s;
@@ -74,8 +74,7 @@ void fill_table(std::vector<uint2> &t, uint32_t p, uint32_t pp, uint32_t g, int 
         pw[0] = 1;
         for (uint32_t e = 1; e < m; e++) pw[e] = host_mulmod(pw[e - 1], w, p);
         for (uint32_t i = 0; i < m; i++) {
-            const uint32_t wm = host_to_mont(pw[bitrev(i, s)], p);
-            t[m + i] = make_uint2(wm, wm * pp);
+            t[m + i] = host_to_mont(pw[bitrev(i, s)], p);
         }
     }
 }
@@ -105,17 +104,17 @@ int get_table(uint32_t p, int log2n, const TwTable **out)
     t->p_prime = host_neg_inv32(p);
     t->log2max = lg;
     t->g = host_primitive_root(p);
-    std::vector<uint2> h;
-    const size_t bytes = (size_t{1} << lg) * sizeof(uint2);
+    std::vector<uint32_t> h;
+    const size_t bytes = (size_t{1} << lg) * sizeof(uint32_t);
     if (cudaMalloc(&t->fwd, bytes) != cudaSuccess || cudaMalloc(&t->inv, bytes) != cudaSuccess) {
         cudaFree(t->fwd);
         delete t;
         cudaGetLastError();
         return MONT_ENOMEM;
     }
-    fill_table(h, p, t->p_prime, t->g, lg, false);
+    fill_table(h, p, t->g, lg, false);
     cudaError_t e1 = cudaMemcpy(t->fwd, h.data(), bytes, cudaMemcpyHostToDevice);
-    fill_table(h, p, t->p_prime, t->g, lg, true);
+    fill_table(h, p, t->g, lg, true);
     cudaError_t e2 = cudaMemcpy(t->inv, h.data(), bytes, cudaMemcpyHostToDevice);
     if (e1 != cudaSuccess || e2 != cudaSuccess) {
         cudaFree(t->fwd);
