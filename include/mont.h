@@ -175,6 +175,74 @@ int polymul_many_ws(uint32_t p, const uint32_t *a, size_t la, const uint32_t *b,
 int polymul_noalloc(const ntt_plan *plan, const uint32_t *a, size_t la, const uint32_t *b, size_t lb,
                     uint32_t *c, cudaStream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Uneven batches: many products of different lengths and primes in one
+ * persistent kernel launch (optionally a CUDA graph replay).
+ * ------------------------------------------------------------------------ */
+
+/* One product of a batch: c[0 .. la+lb-1) = a * b mod p.  a, b, c are device
+ * pointers (c must not overlap a or b); p prime, 3 <= p < 2^31;
+ * la + lb - 1 <= 2^21 and 2^ceil(log2(la+lb-1)) must divide p - 1. */
+typedef struct polymul_desc {
+    const uint32_t *a;
+    const uint32_t *b;
+    uint32_t *c;
+    uint32_t la;
+    uint32_t lb;
+    uint32_t p;
+    uint32_t reserved;   /* must be 0 */
+} polymul_desc;
+
+/* Launch shape of a batch: CTAs per SM of the persistent grid (0 = as many
+ * as fit) and the job order (0: split products' column tiles first, then
+ * the whole small products, then rows and output tiles; 1: small products
+ * first).  Chosen by polymul_batch_plan_tune. */
+typedef struct polymul_batch_config {
+    int ctas_per_sm;
+    int order;
+} polymul_batch_config;
+
+/* Library-owned plan: device copies of the job list and the product table,
+ * synchronisation counters, scratch (2N words per product with N > 2^12),
+ * resident twiddle tables and, once used, a CUDA graph.  Creation allocates
+ * and copies synchronously (not during stream capture).  Up to 8 distinct
+ * primes per batch (else MONT_EUNSUPPORTED). */
+typedef struct polymul_batch_plan polymul_batch_plan;
+
+int polymul_batch_plan_create(const polymul_desc *descs, size_t count, polymul_batch_plan **out);
+void polymul_batch_plan_destroy(polymul_batch_plan *plan);
+size_t polymul_batch_plan_workspace_bytes(const polymul_batch_plan *plan);
+int polymul_batch_plan_get_config(const polymul_batch_plan *plan, polymul_batch_config *cfg);
+int polymul_batch_plan_set_config(polymul_batch_plan *plan, const polymul_batch_config *cfg);
+
+/* Queue the whole batch on `stream`: one memset of the counters and one
+ * persistent kernel launch.  The operands must be ready when it runs. */
+int polymul_batch_run(polymul_batch_plan *plan, cudaStream_t stream);
+
+/* Same work replayed from a CUDA graph captured on first use (re-captured
+ * when the configuration changes). */
+int polymul_batch_run_graph(polymul_batch_plan *plan, cudaStream_t stream);
+
+/* Synchronises `stream`, then reports MONT_OK, or MONT_ETIMEOUT when a
+ * bounded wait inside the last run of the plan expired (its results are
+ * then incomplete; the device context stays usable). */
+int polymul_batch_status(polymul_batch_plan *plan, cudaStream_t stream);
+
+/* Autotuner: runs the batch `trials` times per launch shape (CTAs per SM x
+ * job order), keeps the fastest (CUDA-event timed on `stream`) and caches it
+ * for batches with the same size histogram on this device; synchronous.
+ * Returns the status of the last run. */
+int polymul_batch_plan_tune(polymul_batch_plan *plan, cudaStream_t stream, int trials);
+
+/* Bound of every device-side wait of the plan (default 2^22 polls, 2 s). */
+int polymul_batch_plan_set_wait_limit(polymul_batch_plan *plan, uint32_t iterations, uint64_t nanoseconds);
+
+/* Failure-detection test hook: makes the first split product wait for a
+ * column tile that does not exist, so its bounded waits expire and
+ * polymul_batch_status reports MONT_ETIMEOUT.  MONT_EINVAL if the batch has
+ * no product with N > 2^12. */
+int polymul_batch_plan_inject_stall(polymul_batch_plan *plan);
+
 /* Frees the library-owned scratch buffers (waits for the device). */
 int mont_release_workspaces(void);
 

@@ -90,8 +90,44 @@ def _declare_ntt(L):
     L.polymul_workspace_bytes.restype = _sz
     L.polymul_noalloc.argtypes = [_vp, _vp, _sz, _vp, _sz, _vp, _vp]
     L.polymul_noalloc.restype = ctypes.c_int
+    _declare_batch(L)
     L.mont_release_workspaces.argtypes = []
     L.mont_release_workspaces.restype = ctypes.c_int
+
+
+class PolymulDesc(ctypes.Structure):
+    """Mirror of ``polymul_desc``."""
+    _fields_ = [("a", _vp), ("b", _vp), ("c", _vp), ("la", ctypes.c_uint32), ("lb", ctypes.c_uint32),
+                ("p", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class PolymulBatchConfig(ctypes.Structure):
+    """Mirror of ``polymul_batch_config``."""
+    _fields_ = [("ctas_per_sm", ctypes.c_int), ("order", ctypes.c_int)]
+
+    def __repr__(self):
+        return "PolymulBatchConfig(ctas_per_sm=%d, order=%d)" % (self.ctas_per_sm, self.order)
+
+
+def _declare_batch(L):
+    vpp = ctypes.POINTER(_vp)
+    L.polymul_batch_plan_create.argtypes = [ctypes.POINTER(PolymulDesc), _sz, vpp]
+    L.polymul_batch_plan_destroy.argtypes = [_vp]
+    L.polymul_batch_plan_destroy.restype = None
+    L.polymul_batch_plan_workspace_bytes.argtypes = [_vp]
+    L.polymul_batch_plan_workspace_bytes.restype = _sz
+    L.polymul_batch_plan_get_config.argtypes = [_vp, ctypes.POINTER(PolymulBatchConfig)]
+    L.polymul_batch_plan_set_config.argtypes = [_vp, ctypes.POINTER(PolymulBatchConfig)]
+    L.polymul_batch_run.argtypes = [_vp, _vp]
+    L.polymul_batch_run_graph.argtypes = [_vp, _vp]
+    L.polymul_batch_status.argtypes = [_vp, _vp]
+    L.polymul_batch_plan_tune.argtypes = [_vp, _vp, ctypes.c_int]
+    L.polymul_batch_plan_set_wait_limit.argtypes = [_vp, ctypes.c_uint32, ctypes.c_uint64]
+    L.polymul_batch_plan_inject_stall.argtypes = [_vp]
+    for name in ("polymul_batch_plan_create", "polymul_batch_plan_get_config", "polymul_batch_plan_set_config",
+                 "polymul_batch_run", "polymul_batch_run_graph", "polymul_batch_status", "polymul_batch_plan_tune",
+                 "polymul_batch_plan_set_wait_limit", "polymul_batch_plan_inject_stall"):
+        getattr(L, name).restype = ctypes.c_int
 
 
 def strerror(code):
@@ -301,3 +337,76 @@ def polymul_noalloc(plan, a, b, out=None, stream=None):
     _check(lib().polymul_noalloc(plan.handle, _dev_ptr(a, "a"), a.numel(), _dev_ptr(b, "b"), b.numel(),
                                  _dev_ptr(out, "out"), _stream_handle(stream, a.device)), "polymul_noalloc")
     return out
+
+
+class PolymulBatchPlan:
+    """Owner of a ``polymul_batch_plan *``: an uneven batch of products run by
+    one persistent kernel launch (or a CUDA graph replay of it)."""
+
+    def __init__(self, descs, keepalive=()):
+        arr = (PolymulDesc * max(1, len(descs)))()
+        for i, d in enumerate(descs):
+            arr[i] = d
+        h = _vp()
+        _check(lib().polymul_batch_plan_create(arr, len(descs), ctypes.byref(h)), "polymul_batch_plan_create")
+        self._h = h
+        self._keep = tuple(keepalive)
+        self.count = len(descs)
+
+    @classmethod
+    def from_packed(cls, primes, a, a_off, la, b, b_off, lb, c, c_off):
+        """Products packed back to back: product i uses a[a_off[i]:][:la[i]] etc.
+        (a, b, c int32/uint32 CUDA tensors; offsets and lengths host sequences)."""
+        pa, pb, pc = _dev_ptr(a, "a"), _dev_ptr(b, "b"), _dev_ptr(c, "c")
+        descs = [PolymulDesc(pa + 4 * int(ao), pb + 4 * int(bo), pc + 4 * int(co), int(x), int(y), int(p), 0)
+                 for p, ao, x, bo, y, co in zip(primes, a_off, la, b_off, lb, c_off)]
+        return cls(descs, keepalive=(a, b, c))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def workspace_bytes(self):
+        return int(lib().polymul_batch_plan_workspace_bytes(self._h))
+
+    @property
+    def config(self):
+        c = PolymulBatchConfig()
+        _check(lib().polymul_batch_plan_get_config(self._h, ctypes.byref(c)), "polymul_batch_plan_get_config")
+        return c
+
+    @config.setter
+    def config(self, cfg):
+        _check(lib().polymul_batch_plan_set_config(self._h, ctypes.byref(cfg)), "polymul_batch_plan_set_config")
+
+    def run(self, stream=None, device=None):
+        _check(lib().polymul_batch_run(self._h, _stream_handle(stream, device)), "polymul_batch_run")
+
+    def run_graph(self, stream=None, device=None):
+        _check(lib().polymul_batch_run_graph(self._h, _stream_handle(stream, device)), "polymul_batch_run_graph")
+
+    def status(self, stream=None, device=None):
+        """Synchronise and return MONT_OK or MONT_ETIMEOUT (no exception)."""
+        return lib().polymul_batch_status(self._h, _stream_handle(stream, device))
+
+    def tune(self, trials=3, stream=None, device=None):
+        rc = lib().polymul_batch_plan_tune(self._h, _stream_handle(stream, device), int(trials))
+        _check(rc, "polymul_batch_plan_tune")
+        return self.config
+
+    def set_wait_limit(self, iterations, nanoseconds):
+        _check(lib().polymul_batch_plan_set_wait_limit(self._h, int(iterations), int(nanoseconds)),
+               "polymul_batch_plan_set_wait_limit")
+
+    def inject_stall(self):
+        _check(lib().polymul_batch_plan_inject_stall(self._h), "polymul_batch_plan_inject_stall")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.polymul_batch_plan_destroy(h)
+            self._h = None
+
+
+def polymul_batch_plan_create(descs, keepalive=()):
+    return PolymulBatchPlan(descs, keepalive)

@@ -1,0 +1,659 @@
+// polymul_batch.cu -- many products of uneven sizes and mixed primes in ONE
+// persistent kernel launch (optionally replayed as a CUDA graph).
+//
+// The host turns the batch into a job list.  A product with N <= 2^12 is
+// computed whole by one team of threads (SMALL job; a job covers as many
+// products of one size as fit in a 256-thread CTA).  A product with
+// N = 2^K > 2^12 is split as in ntt_large.cu (K1 = K - 12 column levels,
+// rows of 2^12): COLF jobs run the forward column levels of both operands on
+// one column tile, ROW jobs run one row (forward row levels, pointwise
+// product, inverse row levels), COLI jobs run the inverse column levels of
+// one tile and write c.  Scratch: 2N words per large product.
+//
+// CTAs of the persistent grid claim jobs in list order with one atomic
+// counter.  A ROW job waits until every COLF tile of its product has
+// finished, a COLI job until every ROW of its product has; both waits only
+// depend on jobs earlier in the list, which were claimed by running CTAs,
+// so the grid always makes progress.  Each wait is bounded (iterations and
+// elapsed time); on expiry the CTA sets the error word, skips the job and
+// the host reports MONT_ETIMEOUT.
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "ntt_kernels.cuh"
+
+namespace mont {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kRowLog = 12;        // row size 2^12 for split products
+constexpr int kMaxColLog = 9;      // K1 <= 9: N <= 2^21 in a batch
+constexpr int kMaxPrimes = 8;
+
+enum : uint32_t { JOB_SMALL = 0, JOB_COLF = 1, JOB_ROW = 2, JOB_COLI = 3 };
+
+struct Job {
+    uint32_t type, k, prod, idx;   // idx: tile / row index, or the number of products of a SMALL job
+};
+
+struct Prod {
+    const uint32_t *a, *b;
+    uint32_t *c;
+    uint32_t *ws;         // 2N words, large products only
+    uint32_t la, lb, lc, k;
+    uint32_t prime, k_scale;
+    uint32_t ntiles, nrows;
+};
+
+struct PrimeInfo {
+    uint32_t p, pp;
+    const uint32_t *tw, *itw;
+};
+
+struct BatchArgs {
+    const Job *jobs;
+    const Prod *prods;
+    uint32_t *sync;    // [0] job counter, [1] error word, then per product: COLF done, ROW done
+    uint32_t njobs;
+    uint32_t wait_iters;
+    unsigned long long wait_ns;
+    PrimeInfo primes[kMaxPrimes];
+};
+
+// Column tile geometry for a 256-thread CTA: C columns of N1 = 2^K1, NT1
+// threads per column; layouts chosen (as in ntt_large.cu) for conflict-free
+// tile loads and nearly conflict-free pass accesses.
+template <int K1>
+struct Col256 {
+    static constexpr int N1 = 1 << K1;
+    static constexpr int NT1 = N1 <= 16 ? 1 : N1 / 16;
+    static constexpr int C = kThreads / NT1;
+    static constexpr int PAD = K1 <= 4 ? 1 : 0;
+    static constexpr int MUL = K1 <= 4 ? 0 : ((K1 == 5 || K1 == 8) ? 17 : 9);
+    static constexpr bool SW = K1 >= 8;
+    static constexpr int STRIDE = N1 + PAD;
+    static constexpr int WORDS = C * STRIDE;
+};
+
+constexpr int kSmemWords = 2 * 4352 > 2 * (1 << kRowLog) ? 2 * 4352 : 2 * (1 << kRowLog);
+
+__device__ __forceinline__ unsigned long long globaltimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Thread 0 only: wait until *ctr >= target, bounded by iterations and time.
+// Gives up at once when another CTA has already recorded an expired wait, so
+// a failed batch costs at most about one wait limit in total.
+__device__ bool bounded_wait(const uint32_t *ctr, uint32_t target, const BatchArgs &A)
+{
+    const uint32_t *err = A.sync + 1;
+    const unsigned long long t0 = globaltimer();
+    for (uint32_t it = 0;; it++) {
+        if (ld_acquire(ctr) >= target) return true;
+        if (ld_acquire(err) != 0u || it >= A.wait_iters || globaltimer() - t0 > A.wait_ns) return false;
+        __nanosleep(200);
+    }
+}
+
+template <int K1, bool INV>
+__device__ __forceinline__ void col_tile(uint32_t *smem, const Prod &P, const PrimeInfo &pr, uint32_t tile)
+{
+    using CF = Col256<K1>;
+    constexpr int NP = Sched<K1>::kPasses;
+    constexpr int NARR = INV ? 1 : 2;
+    const size_t n = size_t{1} << P.k;
+    const size_t o0 = static_cast<size_t>(tile) * CF::C;
+    const Mod md{pr.p, pr.pp};
+    auto col = [&](int a, int c) {
+        return ColLayout<CF::SW>{smem + a * CF::WORDS + c * CF::STRIDE, (c * CF::MUL) & 31};
+    };
+#pragma unroll
+    for (int a = 0; a < NARR; a++) {
+        const uint32_t *src = INV ? P.ws : (a ? P.b : P.a);
+        const size_t slen = INV ? n : (a ? P.lb : P.la);
+        for (int i = threadIdx.x; i < CF::C * CF::N1; i += kThreads) {
+            const int t = i / CF::C, c = i % CF::C;
+            const size_t j = o0 + c + (static_cast<size_t>(t) << kRowLog);
+            uint32_t v = j < slen ? __ldg(src + j) : 0u;
+            if (!INV && a == 1) v = mont_mul(v, P.k_scale, pr.p, pr.pp);
+            col(a, c)[t] = v;
+        }
+    }
+    __syncthreads();
+    const int c = threadIdx.x / CF::NT1, tid = threadIdx.x % CF::NT1;
+    if constexpr (!INV) {
+        const ColLayout<CF::SW> lay[2] = {col(0, c), col(1, c)};
+        fwd_passes<K1, CF::NT1, 2, true, 0, NP - 1>(lay, tid, pr.tw, 0, 0, md);
+    } else {
+        inv_passes<K1, CF::NT1, true, NP - 1, 0>(col(0, c), tid, pr.itw, 0, 0, md);
+    }
+#pragma unroll
+    for (int a = 0; a < NARR; a++) {
+        uint32_t *dst = INV ? P.c : P.ws + a * n;
+        const size_t dlen = INV ? P.lc : n;
+        for (int i = threadIdx.x; i < CF::C * CF::N1; i += kThreads) {
+            const int t = i / CF::C, cc = i % CF::C;
+            const size_t j = o0 + cc + (static_cast<size_t>(t) << kRowLog);
+            if (j < dlen) dst[j] = col(a, cc)[t];
+        }
+    }
+}
+
+template <bool INV>
+__device__ __forceinline__ void col_job(uint32_t *smem, const Prod &P, const PrimeInfo &pr, uint32_t tile)
+{
+    switch (P.k - kRowLog) {
+    case 1: col_tile<1, INV>(smem, P, pr, tile); break;
+    case 2: col_tile<2, INV>(smem, P, pr, tile); break;
+    case 3: col_tile<3, INV>(smem, P, pr, tile); break;
+    case 4: col_tile<4, INV>(smem, P, pr, tile); break;
+    case 5: col_tile<5, INV>(smem, P, pr, tile); break;
+    case 6: col_tile<6, INV>(smem, P, pr, tile); break;
+    case 7: col_tile<7, INV>(smem, P, pr, tile); break;
+    case 8: col_tile<8, INV>(smem, P, pr, tile); break;
+    case 9: col_tile<9, INV>(smem, P, pr, tile); break;
+    default: break;
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void small_job(uint32_t *smem, const BatchArgs &A, const Job &J)
+{
+    constexpr int NT = nt_of<K>(), T = kThreads / NT, N = 1 << K;
+    const int team = threadIdx.x / NT, tid = threadIdx.x - team * NT;
+    const bool valid = static_cast<uint32_t>(team) < J.idx;
+    const Prod &P = A.prods[J.prod + (valid ? team : 0)];
+    const PrimeInfo &pr = A.primes[P.prime];
+    static_assert(T * 2 * N <= kSmemWords, "small job does not fit");
+    polymul_team<K, true, true>(smem + team * 2 * N, tid, P.a, valid ? P.la : 0, P.b, valid ? P.lb : 0, P.c,
+                                valid ? P.lc : 0, pr.tw, pr.itw, 0, 0, pr.p, pr.pp, P.k_scale);
+}
+
+__device__ __forceinline__ void small_dispatch(uint32_t *smem, const BatchArgs &A, const Job &J)
+{
+    switch (J.k) {
+    case 0: small_job<0>(smem, A, J); break;
+    case 1: small_job<1>(smem, A, J); break;
+    case 2: small_job<2>(smem, A, J); break;
+    case 3: small_job<3>(smem, A, J); break;
+    case 4: small_job<4>(smem, A, J); break;
+    case 5: small_job<5>(smem, A, J); break;
+    case 6: small_job<6>(smem, A, J); break;
+    case 7: small_job<7>(smem, A, J); break;
+    case 8: small_job<8>(smem, A, J); break;
+    case 9: small_job<9>(smem, A, J); break;
+    case 10: small_job<10>(smem, A, J); break;
+    case 11: small_job<11>(smem, A, J); break;
+    case 12: small_job<12>(smem, A, J); break;
+    default: break;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 2) k_polymul_batch(BatchArgs A)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ uint32_t s_job;
+    __shared__ int s_ok;
+    uint32_t *err = A.sync + 1;
+    for (;;) {
+        if (threadIdx.x == 0) s_job = atomicAdd(A.sync, 1u);
+        __syncthreads();
+        const uint32_t jid = s_job;
+        if (jid >= A.njobs) break;
+        const Job J = A.jobs[jid];
+        if (J.type == JOB_SMALL) {
+            small_dispatch(smem, A, J);
+        } else {
+            const Prod &P = A.prods[J.prod];
+            const PrimeInfo &pr = A.primes[P.prime];
+            uint32_t *done = A.sync + 2 + 2 * static_cast<size_t>(J.prod);
+            if (J.type != JOB_COLF && threadIdx.x == 0) {
+                const bool ok = J.type == JOB_ROW ? bounded_wait(done, P.ntiles, A)
+                                                  : bounded_wait(done + 1, P.nrows, A);
+                if (!ok) atomicOr(err, 1u);
+                s_ok = ok;
+            }
+            __syncthreads();
+            const bool ok = J.type == JOB_COLF || s_ok;
+            if (ok) {
+                __threadfence();
+                if (J.type == JOB_COLF) {
+                    col_job<false>(smem, P, pr, J.idx);
+                } else if (J.type == JOB_ROW) {
+                    uint32_t *row = P.ws + (static_cast<size_t>(J.idx) << kRowLog);
+                    const size_t n = size_t{1} << P.k;
+                    polymul_team<kRowLog, false, false>(smem, threadIdx.x, row, size_t{1} << kRowLog, row + n,
+                                                        size_t{1} << kRowLog, row, size_t{1} << kRowLog, pr.tw,
+                                                        pr.itw, static_cast<int>(P.k) - kRowLog,
+                                                        static_cast<int>(J.idx), pr.p, pr.pp, 0u);
+                } else {
+                    col_job<true>(smem, P, pr, J.idx);
+                }
+            }
+            __syncthreads();
+            if (ok && threadIdx.x == 0 && J.type != JOB_COLI) {
+                __threadfence();
+                atomicAdd(J.type == JOB_COLF ? done : done + 1, 1u);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+int col_tiles(int k1)
+{
+    const int nt1 = k1 <= 4 ? 1 : (1 << k1) / 16;
+    const int c = kThreads / nt1;
+    return (1 << kRowLog) / c;
+}
+
+int teams_for(int k)
+{
+    const int nt = k <= 4 ? 1 : (1 << (k - 4));
+    return kThreads / nt;
+}
+
+}  // namespace
+}  // namespace mont
+
+struct polymul_batch_plan {
+    int device = 0;
+    size_t count = 0;
+    std::vector<mont::Prod> prods;       // host copy (device pointers inside)
+    std::vector<uint32_t> prime_list;
+    std::vector<int> prime_log2;
+    mont::BatchArgs args{};
+    std::vector<mont::Job> jobs[2];       // per job order policy
+    mont::Job *d_jobs[2] = {nullptr, nullptr};
+    mont::Prod *d_prods = nullptr;
+    uint32_t *d_sync = nullptr;
+    size_t sync_words = 0;
+    uint32_t *d_ws = nullptr;
+    size_t ws_words = 0;
+    int occupancy = 1;
+    int sms = 1;
+    polymul_batch_config cfg{};
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    polymul_batch_config graph_cfg{};
+};
+
+namespace mont {
+namespace {
+
+std::mutex g_tune_mu;
+std::map<std::string, polymul_batch_config> g_tune_cache;
+
+std::string signature(const polymul_batch_plan *pl)
+{
+    std::map<uint32_t, size_t> hist;
+    for (const Prod &P : pl->prods) hist[P.k]++;
+    std::string s = std::to_string(pl->device) + ":";
+    for (auto &kv : hist) s += std::to_string(kv.first) + "x" + std::to_string(kv.second) + ",";
+    return s;
+}
+
+void build_jobs(polymul_batch_plan *pl, const std::vector<size_t> &small_order, const std::vector<size_t> &large)
+{
+    for (int order = 0; order < 2; order++) {
+        std::vector<Job> &jobs = pl->jobs[order];
+        jobs.clear();
+        std::vector<Job> colf, small, row, coli;
+        for (size_t i : large) {
+            const Prod &P = pl->prods[i];
+            for (uint32_t t = 0; t < P.ntiles; t++) colf.push_back(Job{JOB_COLF, P.k, static_cast<uint32_t>(i), t});
+            for (uint32_t r = 0; r < P.nrows; r++) row.push_back(Job{JOB_ROW, P.k, static_cast<uint32_t>(i), r});
+            for (uint32_t t = 0; t < P.ntiles; t++) coli.push_back(Job{JOB_COLI, P.k, static_cast<uint32_t>(i), t});
+        }
+        for (size_t s = 0; s < small_order.size();) {
+            const uint32_t k = pl->prods[small_order[s]].k;
+            const size_t per = static_cast<size_t>(teams_for(static_cast<int>(k)));
+            size_t e = s;
+            while (e < small_order.size() && e - s < per && pl->prods[small_order[e]].k == k) e++;
+            small.push_back(Job{JOB_SMALL, k, static_cast<uint32_t>(small_order[s]), static_cast<uint32_t>(e - s)});
+            s = e;
+        }
+        if (order == 0) {   // large products' column tiles first, small products fill the gaps
+            jobs.insert(jobs.end(), colf.begin(), colf.end());
+            jobs.insert(jobs.end(), small.begin(), small.end());
+            jobs.insert(jobs.end(), row.begin(), row.end());
+            jobs.insert(jobs.end(), coli.begin(), coli.end());
+        } else {            // small products first, large products phase by phase
+            jobs.insert(jobs.end(), small.begin(), small.end());
+            jobs.insert(jobs.end(), colf.begin(), colf.end());
+            jobs.insert(jobs.end(), row.begin(), row.end());
+            jobs.insert(jobs.end(), coli.begin(), coli.end());
+        }
+    }
+}
+
+void free_plan(polymul_batch_plan *pl)
+{
+    if (pl->graph) cudaGraphExecDestroy(pl->graph);
+    if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
+    cudaFree(pl->d_jobs[0]);
+    cudaFree(pl->d_jobs[1]);
+    cudaFree(pl->d_prods);
+    cudaFree(pl->d_sync);
+    cudaFree(pl->d_ws);
+}
+
+int launch(polymul_batch_plan *pl, const polymul_batch_config &cfg, cudaStream_t s)
+{
+    BatchArgs A = pl->args;
+    const int order = cfg.order == 1 ? 1 : 0;
+    A.jobs = pl->d_jobs[order];
+    A.njobs = static_cast<uint32_t>(pl->jobs[order].size());
+    if (cudaMemsetAsync(pl->d_sync, 0, pl->sync_words * sizeof(uint32_t), s) != cudaSuccess) return MONT_ECUDA;
+    if (A.njobs == 0) return MONT_OK;
+    const int per_sm = std::max(1, std::min(cfg.ctas_per_sm > 0 ? cfg.ctas_per_sm : pl->occupancy, pl->occupancy));
+    const size_t grid = std::min<size_t>(static_cast<size_t>(pl->sms) * per_sm, A.njobs);
+    k_polymul_batch<<<static_cast<unsigned>(grid), kThreads, kSmemWords * sizeof(uint32_t), s>>>(A);
+    return launch_status();
+}
+
+}  // namespace
+}  // namespace mont
+
+extern "C" int polymul_batch_plan_create(const polymul_desc *descs, size_t count, polymul_batch_plan **out)
+{
+    using namespace mont;
+    if (!out || (count && !descs)) return MONT_EINVAL;
+    *out = nullptr;
+    if (count > (size_t{1} << 31)) return MONT_ERANGE;
+    polymul_batch_plan *pl = new (std::nothrow) polymul_batch_plan();
+    if (!pl) return MONT_ENOMEM;
+    if (cudaGetDevice(&pl->device) != cudaSuccess) {
+        delete pl;
+        return MONT_ECUDA;
+    }
+    pl->count = count;
+    pl->prods.resize(count);
+    std::vector<size_t> small, large;
+    size_t ws_words = 0;
+    int rc = MONT_OK;
+    for (size_t i = 0; i < count && rc == MONT_OK; i++) {
+        const polymul_desc &d = descs[i];
+        if (!d.a || !d.b || !d.c || d.la == 0 || d.lb == 0 || d.reserved != 0) rc = MONT_EINVAL;
+        else if (d.la > (1u << 24) || d.lb > (1u << 24)) rc = MONT_ERANGE;
+        if (rc != MONT_OK) break;
+        const size_t lc = static_cast<size_t>(d.la) + d.lb - 1;
+        const int k = ceil_log2(lc);
+        if (k > kRowLog + kMaxColLog) {
+            rc = MONT_EUNSUPPORTED;
+            break;
+        }
+        if (any_overlap(d.c, lc * 4, d.a, size_t{d.la} * 4) || any_overlap(d.c, lc * 4, d.b, size_t{d.lb} * 4)) {
+            rc = MONT_EINVAL;
+            break;
+        }
+        size_t pi = 0;
+        while (pi < pl->prime_list.size() && pl->prime_list[pi] != d.p) pi++;
+        if (pi == pl->prime_list.size()) {
+            if (pi == kMaxPrimes) {
+                rc = MONT_EUNSUPPORTED;
+                break;
+            }
+            pl->prime_list.push_back(d.p);
+            pl->prime_log2.push_back(0);
+        }
+        pl->prime_log2[pi] = std::max(pl->prime_log2[pi], k);
+        Prod &P = pl->prods[i];
+        P.a = d.a;
+        P.b = d.b;
+        P.c = d.c;
+        P.ws = nullptr;
+        P.la = d.la;
+        P.lb = d.lb;
+        P.lc = static_cast<uint32_t>(lc);
+        P.k = static_cast<uint32_t>(k);
+        P.prime = static_cast<uint32_t>(pi);
+        const uint32_t n_mod = static_cast<uint32_t>((uint64_t{1} << k) % d.p);
+        P.k_scale = host_to_mont(host_to_mont(host_powmod(n_mod, d.p - 2, d.p), d.p), d.p);   // N^-1 R^2
+        P.ntiles = P.nrows = 0;
+        if (k > kRowLog) {
+            P.ntiles = static_cast<uint32_t>(col_tiles(k - kRowLog));
+            P.nrows = 1u << (k - kRowLog);
+            P.ws = reinterpret_cast<uint32_t *>(ws_words);   // offset, rebased below
+            ws_words += size_t{2} << k;
+            large.push_back(i);
+        } else {
+            small.push_back(i);
+        }
+    }
+    if (rc == MONT_OK) {
+        for (size_t pi = 0; pi < pl->prime_list.size() && rc == MONT_OK; pi++) {
+            const TwTable *t = nullptr;
+            rc = get_table(pl->prime_list[pi], std::max(pl->prime_log2[pi], kRowLog), &t);
+            if (rc == MONT_OK) {
+                pl->args.primes[pi] = PrimeInfo{t->p, t->p_prime, t->fwd, t->inv};
+            }
+        }
+    }
+    if (rc != MONT_OK) {
+        delete pl;
+        return rc;
+    }
+    std::stable_sort(small.begin(), small.end(),
+                     [&](size_t x, size_t y) { return pl->prods[x].k < pl->prods[y].k; });
+    // SMALL jobs reference consecutive product indices: store the products
+    // in job order (small ones sorted by size, then the large ones).
+    std::vector<Prod> ordered;
+    ordered.reserve(count);
+    std::vector<size_t> small_idx, large_idx;
+    for (size_t i : small) {
+        small_idx.push_back(ordered.size());
+        ordered.push_back(pl->prods[i]);
+    }
+    for (size_t i : large) {
+        large_idx.push_back(ordered.size());
+        ordered.push_back(pl->prods[i]);
+    }
+    pl->prods.swap(ordered);
+    build_jobs(pl, small_idx, large_idx);
+
+    bool ok = true;
+    pl->ws_words = ws_words;
+    pl->sync_words = 2 + 2 * count;
+    ok = ok && cudaMalloc(&pl->d_sync, pl->sync_words * sizeof(uint32_t)) == cudaSuccess &&
+         cudaMemset(pl->d_sync, 0, pl->sync_words * sizeof(uint32_t)) == cudaSuccess;
+    if (ws_words) ok = ok && cudaMalloc(&pl->d_ws, ws_words * sizeof(uint32_t)) == cudaSuccess;
+    if (ok) {
+        for (Prod &P : pl->prods)
+            if (P.k > static_cast<uint32_t>(kRowLog)) P.ws = pl->d_ws + reinterpret_cast<size_t>(P.ws);
+    }
+    if (ok && count) ok = cudaMalloc(&pl->d_prods, count * sizeof(Prod)) == cudaSuccess &&
+                          cudaMemcpy(pl->d_prods, pl->prods.data(), count * sizeof(Prod), cudaMemcpyHostToDevice) ==
+                              cudaSuccess;
+    for (int o = 0; o < 2 && ok; o++)
+        if (!pl->jobs[o].empty())
+            ok = cudaMalloc(&pl->d_jobs[o], pl->jobs[o].size() * sizeof(Job)) == cudaSuccess &&
+                 cudaMemcpy(pl->d_jobs[o], pl->jobs[o].data(), pl->jobs[o].size() * sizeof(Job),
+                            cudaMemcpyHostToDevice) == cudaSuccess;
+    if (ok) ok = cudaFuncSetAttribute(k_polymul_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      kSmemWords * sizeof(uint32_t)) == cudaSuccess;
+    if (ok) ok = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pl->occupancy, k_polymul_batch, kThreads,
+                                                               kSmemWords * sizeof(uint32_t)) == cudaSuccess;
+    pl->sms = device_sm_count();
+    if (!ok || pl->sms <= 0 || pl->occupancy <= 0) {
+        cudaGetLastError();
+        free_plan(pl);
+        delete pl;
+        return MONT_ENOMEM;
+    }
+    pl->args.prods = pl->d_prods;
+    pl->args.sync = pl->d_sync;
+    pl->args.wait_iters = 1u << 22;
+    pl->args.wait_ns = 2000000000ull;   // 2 s per wait
+    pl->cfg.ctas_per_sm = pl->occupancy;
+    pl->cfg.order = 0;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(signature(pl));
+        if (it != g_tune_cache.end()) pl->cfg = it->second;
+    }
+    *out = pl;
+    return MONT_OK;
+}
+
+extern "C" void polymul_batch_plan_destroy(polymul_batch_plan *plan)
+{
+    if (!plan) return;
+    mont::free_plan(plan);
+    delete plan;
+}
+
+extern "C" size_t polymul_batch_plan_workspace_bytes(const polymul_batch_plan *plan)
+{
+    return plan ? plan->ws_words * sizeof(uint32_t) : 0;
+}
+
+extern "C" int polymul_batch_plan_get_config(const polymul_batch_plan *plan, polymul_batch_config *cfg)
+{
+    if (!plan || !cfg) return MONT_EINVAL;
+    *cfg = plan->cfg;
+    return MONT_OK;
+}
+
+extern "C" int polymul_batch_plan_set_config(polymul_batch_plan *plan, const polymul_batch_config *cfg)
+{
+    if (!plan || !cfg || cfg->ctas_per_sm < 0 || cfg->order < 0 || cfg->order > 1) return MONT_EINVAL;
+    plan->cfg = *cfg;
+    return MONT_OK;
+}
+
+extern "C" int polymul_batch_plan_set_wait_limit(polymul_batch_plan *plan, uint32_t iterations, uint64_t nanoseconds)
+{
+    if (!plan || iterations == 0 || nanoseconds == 0) return MONT_EINVAL;
+    plan->args.wait_iters = iterations;
+    plan->args.wait_ns = nanoseconds;
+    if (plan->graph) {
+        cudaGraphExecDestroy(plan->graph);
+        plan->graph = nullptr;
+    }
+    return MONT_OK;
+}
+
+extern "C" int polymul_batch_run(polymul_batch_plan *plan, cudaStream_t stream)
+{
+    if (!plan) return MONT_EINVAL;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return MONT_ECUDA;
+    if (dev != plan->device) return MONT_EINVAL;
+    return mont::launch(plan, plan->cfg, stream);
+}
+
+extern "C" int polymul_batch_run_graph(polymul_batch_plan *plan, cudaStream_t stream)
+{
+    if (!plan) return MONT_EINVAL;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return MONT_ECUDA;
+    if (dev != plan->device) return MONT_EINVAL;
+    if (plan->graph && (plan->graph_cfg.ctas_per_sm != plan->cfg.ctas_per_sm || plan->graph_cfg.order != plan->cfg.order)) {
+        cudaGraphExecDestroy(plan->graph);
+        plan->graph = nullptr;
+    }
+    if (!plan->graph) {
+        if (!plan->cap_stream && cudaStreamCreateWithFlags(&plan->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+            return MONT_ECUDA;
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(plan->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MONT_ECUDA;
+        const int rc = mont::launch(plan, plan->cfg, plan->cap_stream);
+        const cudaError_t ec = cudaStreamEndCapture(plan->cap_stream, &g);
+        if (rc != MONT_OK || ec != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return rc != MONT_OK ? rc : MONT_ECUDA;
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&plan->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) {
+            plan->graph = nullptr;
+            cudaGetLastError();
+            return MONT_ECUDA;
+        }
+        plan->graph_cfg = plan->cfg;
+    }
+    return cudaGraphLaunch(plan->graph, stream) == cudaSuccess ? MONT_OK : MONT_ECUDA;
+}
+
+// Synchronous: waits for `stream`, then reads the device error word.
+extern "C" int polymul_batch_status(polymul_batch_plan *plan, cudaStream_t stream)
+{
+    if (!plan) return MONT_EINVAL;
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return MONT_ECUDA;
+    uint32_t err = 0;
+    if (cudaMemcpy(&err, plan->d_sync + 1, sizeof(err), cudaMemcpyDeviceToHost) != cudaSuccess) return MONT_ECUDA;
+    return err ? MONT_ETIMEOUT : MONT_OK;
+}
+
+// Autotuner: times every (CTAs per SM, job order) choice `trials` times
+// with CUDA events on `stream` and keeps the fastest; the result is cached
+// for batches with the same size histogram on this device.
+extern "C" int polymul_batch_plan_tune(polymul_batch_plan *plan, cudaStream_t stream, int trials)
+{
+    if (!plan || trials <= 0) return MONT_EINVAL;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return MONT_ECUDA;
+    polymul_batch_config best = plan->cfg;
+    float best_ms = 1e30f;
+    int rc = MONT_OK;
+    for (int per = 1; per <= plan->occupancy && rc == MONT_OK; per++)
+        for (int order = 0; order < 2 && rc == MONT_OK; order++) {
+            polymul_batch_config c{};
+            c.ctas_per_sm = per;
+            c.order = order;
+            rc = mont::launch(plan, c, stream);   // warm-up
+            float total = 0.f;
+            for (int t = 0; t < trials && rc == MONT_OK; t++) {
+                cudaEventRecord(e0, stream);
+                rc = mont::launch(plan, c, stream);
+                cudaEventRecord(e1, stream);
+                if (cudaEventSynchronize(e1) != cudaSuccess) rc = MONT_ECUDA;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                total += ms;
+            }
+            if (rc == MONT_OK && total < best_ms) {
+                best_ms = total;
+                best = c;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != MONT_OK) return rc;
+    plan->cfg = best;
+    std::lock_guard<std::mutex> lock(mont::g_tune_mu);
+    mont::g_tune_cache[mont::signature(plan)] = best;
+    return polymul_batch_status(plan, stream);
+}
+
+// Test hook for failure detection: makes product `index` (a split product)
+// expect one more column tile than exists, so its row jobs wait on a count
+// that is never reached; the bounded waits expire and the batch reports
+// MONT_ETIMEOUT.  Undone by recreating the plan.
+extern "C" int polymul_batch_plan_inject_stall(polymul_batch_plan *plan)
+{
+    if (!plan) return MONT_EINVAL;
+    for (size_t i = 0; i < plan->prods.size(); i++) {
+        if (plan->prods[i].k <= static_cast<uint32_t>(mont::kRowLog)) continue;
+        plan->prods[i].ntiles += 1;
+        if (cudaMemcpy(plan->d_prods + i, &plan->prods[i], sizeof(mont::Prod), cudaMemcpyHostToDevice) != cudaSuccess)
+            return MONT_ECUDA;
+        return MONT_OK;
+    }
+    return MONT_EINVAL;
+}

@@ -1,0 +1,132 @@
+"""GPU parity of the uneven persistent batch (one launch, mixed sizes and
+primes) with the CPU oracle, plus graph replay, autotuning, alone-vs-mix
+equality and the bounded-wait failure path.  All comparisons bit-exact."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1609_00999_gb300 import synth
+
+from helpers import to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def m():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1609_00999_gb300 as m
+    from paper_1609_00999_gb300 import build
+    build.build()
+    return m
+
+
+def run_packed(m, wl, graph=False, tune=False):
+    import torch
+    da, db = to_dev(wl.a), to_dev(wl.b)
+    dc = torch.full((max(1, wl.c_size),), -1, dtype=torch.int32, device="cuda")
+    plan = m.PolymulBatchPlan.from_packed(wl.primes, da, wl.a_off, wl.la, db, wl.b_off, wl.lb, dc, wl.c_off)
+    if tune:
+        plan.tune(trials=1)
+    (plan.run_graph if graph else plan.run)()
+    assert plan.status() == m.MONT_OK
+    return plan, da, db, dc
+
+
+def oracle_packed(wl):
+    return oracle.polymul_batch(wl.primes, wl.a, wl.a_off, wl.la, wl.b, wl.b_off, wl.lb, wl.c_off, wl.c_size,
+                                use_ntt=True)
+
+
+def mixed_batch(seed=600):
+    rng = np.random.default_rng(seed)
+    lens = []
+    for k in range(0, 22):                      # every power-of-two size 2^0 .. 2^21 at least once
+        lo, hi = max(1, (1 << k) // 4), max(1, (1 << k) // 2)
+        lens += [(int(rng.integers(lo, hi + 1)), int(rng.integers(lo, hi + 1)))]
+    lens += [(1, 1), (1, 5000), (3000, 1), (2048, 2048), (2049, 2048), (4096, 4097), (300, 17)]
+    lens += [(int(x), int(x)) for x in synth.loguniform_lengths(200, 1 << 4, 1 << 13, seed, 1)]
+    primes = synth.choose_primes(len(lens), seed, 2)
+    la = [x for x, _ in lens]
+    lb = [y for _, y in lens]
+    return synth.UnevenBatch(primes, la, lb, (seed,))
+
+
+def test_mixed_batch_matches_oracle(m):
+    wl = mixed_batch()
+    plan, _, _, dc = run_packed(m, wl)
+    assert np.array_equal(to_host(dc)[:wl.c_size], oracle_packed(wl))
+
+
+def test_graph_replay_and_tuning_give_identical_results(m):
+    wl = mixed_batch(601)
+    ref = oracle_packed(wl)
+    plan, da, db, dc = run_packed(m, wl, graph=True)
+    assert np.array_equal(to_host(dc)[:wl.c_size], ref)
+    dc.fill_(-1)
+    plan.run_graph()                              # replay: counters are reset by the graph itself
+    assert plan.status() == m.MONT_OK
+    assert np.array_equal(to_host(dc)[:wl.c_size], ref)
+    cfg = plan.tune(trials=1)
+    assert cfg.ctas_per_sm >= 1 and cfg.order in (0, 1)
+    for order in (0, 1):
+        c = m.PolymulBatchConfig(1, order)
+        plan.config = c
+        dc.fill_(-1)
+        plan.run_graph()
+        assert plan.status() == m.MONT_OK
+        assert np.array_equal(to_host(dc)[:wl.c_size], ref)
+
+
+def test_alone_equals_in_the_mix(m):
+    """Every product of a mixed batch equals the same product computed alone."""
+    wl = mixed_batch(602)
+    _, da, db, dc = run_packed(m, wl)
+    got = to_host(dc)
+    for i in range(len(wl)):
+        ao, la = int(wl.a_off[i]), int(wl.la[i])
+        bo, lb = int(wl.b_off[i]), int(wl.lb[i])
+        co = int(wl.c_off[i])
+        alone = to_host(m.polymul(int(wl.primes[i]), da[ao:ao + la], db[bo:bo + lb]))
+        assert np.array_equal(got[co:co + la + lb - 1], alone), i
+
+
+def test_uneven_config_sample(m):
+    """A 600-product slice of the 10,000-product uneven workload (L log-uniform in [2^6, 2^16])."""
+    wl_full = synth.batch_uneven(count=600)
+    plan, _, _, dc = run_packed(m, wl_full, tune=True)
+    assert np.array_equal(to_host(dc)[:wl_full.c_size], oracle_packed(wl_full))
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(m):
+    import torch
+    wl = synth.UnevenBatch([synth.P1, synth.P2], [5000, 10], [5000, 10], (603,))
+    da, db = to_dev(wl.a), to_dev(wl.b)
+    dc = torch.zeros(wl.c_size, dtype=torch.int32, device="cuda")
+    plan = m.PolymulBatchPlan.from_packed(wl.primes, da, wl.a_off, wl.la, db, wl.b_off, wl.lb, dc, wl.c_off)
+    plan.set_wait_limit(20000, 20_000_000)        # 20 ms per wait
+    plan.inject_stall()                           # rows wait for a column tile that never finishes
+    plan.run()
+    assert plan.status() == m.MONT_ETIMEOUT
+    # the context is still usable: a fresh plan of the same batch is exact
+    _, _, _, dc2 = run_packed(m, wl)
+    assert np.array_equal(to_host(dc2)[:wl.c_size], oracle_packed(wl))
+
+
+def test_batch_argument_errors(m):
+    import torch
+    d = to_dev(np.ones(8, dtype=np.uint32))
+    out = torch.zeros(64, dtype=torch.int32, device="cuda")
+    bad = [m.PolymulDesc(d.data_ptr(), d.data_ptr(), out.data_ptr(), 0, 4, synth.P1, 0)]
+    with pytest.raises(m.MontError) as e:
+        m.PolymulBatchPlan(bad)
+    assert e.value.code == m.MONT_EINVAL
+    huge = [m.PolymulDesc(d.data_ptr(), d.data_ptr(), out.data_ptr(), 1 << 21, 1 << 21, synth.P1, 0)]
+    with pytest.raises(m.MontError) as e:
+        m.PolymulBatchPlan(huge)
+    assert e.value.code in (m.MONT_EUNSUPPORTED, m.MONT_ERANGE)
+    empty = m.PolymulBatchPlan([])
+    empty.run()
+    assert empty.status() == m.MONT_OK
