@@ -243,6 +243,64 @@ int polymul_batch_plan_set_wait_limit(polymul_batch_plan *plan, uint32_t iterati
  * no product with N > 2^12. */
 int polymul_batch_plan_inject_stall(polymul_batch_plan *plan);
 
+/* ------------------------------------------------------------------------
+ * Continuous-batching request server (single host thread, one device).
+ * ------------------------------------------------------------------------ */
+
+/* One request: c[0 .. la+lb-1) = a * b mod p.  a, b, c may be host memory
+ * (pinned for asynchronous copies) or device memory; they must stay valid
+ * until the request's completion is reported.  id is returned with it. */
+typedef struct mont_request {
+    const uint32_t *a;
+    const uint32_t *b;
+    uint32_t *c;
+    uint32_t la;
+    uint32_t lb;
+    uint32_t p;
+    uint32_t reserved;   /* must be 0 */
+    uint64_t id;
+} mont_request;
+
+typedef struct mont_completion {
+    uint64_t id;
+    int status;          /* MONT_OK, MONT_ETIMEOUT or MONT_ECUDA */
+    int reserved;
+} mont_completion;
+
+typedef struct mont_server_stats {
+    uint64_t submitted, admitted, launched, completed, batches;   /* running totals */
+    uint64_t queued, admitted_waiting, in_flight;                   /* current requests per stage */
+    uint64_t bytes_in_use, peak_bytes, budget_bytes;                /* device-memory budget */
+} mont_server_stats;
+
+typedef struct mont_server mont_server;
+
+/* Server for the given primes (at most 8; twiddle tables for N up to
+ * 2^max_log2n, max_log2n <= 21, built now and kept resident), a device-memory
+ * budget of budget_bytes (one allocation made now) that holds every admitted
+ * request's operands, result and scratch, `slots` streams (batches in flight
+ * at once) and at most max_batch_coeffs input coefficients per batch (a single
+ * larger request still forms a batch of its own). */
+int mont_server_create(const uint32_t *primes, int nprimes, uint32_t max_log2n, size_t budget_bytes, int slots,
+                       size_t max_batch_coeffs, mont_server **out);
+
+/* Waits for the work in flight, then frees everything. */
+void mont_server_destroy(mont_server *server);
+
+/* Queues n requests (no device work).  The whole call is rejected with
+ * MONT_EINVAL (bad pointer, length, or a prime the server was not created
+ * for) or MONT_ERANGE (N beyond max_log2n, or a request larger than the
+ * whole budget). */
+int mont_server_submit(mont_server *server, const mont_request *reqs, size_t n);
+
+/* Non-blocking step: retires finished batches (their memory returns to the
+ * budget), admits queued requests in order while memory allows, launches the
+ * admitted requests on every idle slot, and copies up to cap completions
+ * into done (*ndone of them).  Call it repeatedly from one thread. */
+int mont_server_progress(mont_server *server, mont_completion *done, size_t cap, size_t *ndone);
+
+int mont_server_get_stats(const mont_server *server, mont_server_stats *out);
+
 /* Frees the library-owned scratch buffers (waits for the device). */
 int mont_release_workspaces(void);
 

@@ -91,6 +91,7 @@ def _declare_ntt(L):
     L.polymul_noalloc.argtypes = [_vp, _vp, _sz, _vp, _sz, _vp, _vp]
     L.polymul_noalloc.restype = ctypes.c_int
     _declare_batch(L)
+    _declare_server(L)
     L.mont_release_workspaces.argtypes = []
     L.mont_release_workspaces.restype = ctypes.c_int
 
@@ -127,6 +128,29 @@ def _declare_batch(L):
     for name in ("polymul_batch_plan_create", "polymul_batch_plan_get_config", "polymul_batch_plan_set_config",
                  "polymul_batch_run", "polymul_batch_run_graph", "polymul_batch_status", "polymul_batch_plan_tune",
                  "polymul_batch_plan_set_wait_limit", "polymul_batch_plan_inject_stall"):
+        getattr(L, name).restype = ctypes.c_int
+
+
+class MontServerStats(ctypes.Structure):
+    """Mirror of ``mont_server_stats``."""
+    _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "admitted", "launched", "completed", "batches", "queued",
+                                               "admitted_waiting", "in_flight", "bytes_in_use", "peak_bytes",
+                                               "budget_bytes")]
+
+    def as_dict(self):
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
+def _declare_server(L):
+    vpp = ctypes.POINTER(_vp)
+    L.mont_server_create.argtypes = [ctypes.POINTER(ctypes.c_uint32), ctypes.c_int, ctypes.c_uint32, _sz,
+                                     ctypes.c_int, _sz, vpp]
+    L.mont_server_destroy.argtypes = [_vp]
+    L.mont_server_destroy.restype = None
+    L.mont_server_submit.argtypes = [_vp, _vp, _sz]
+    L.mont_server_progress.argtypes = [_vp, _vp, _sz, ctypes.POINTER(_sz)]
+    L.mont_server_get_stats.argtypes = [_vp, ctypes.POINTER(MontServerStats)]
+    for name in ("mont_server_create", "mont_server_submit", "mont_server_progress", "mont_server_get_stats"):
         getattr(L, name).restype = ctypes.c_int
 
 
@@ -410,3 +434,56 @@ class PolymulBatchPlan:
 
 def polymul_batch_plan_create(descs, keepalive=()):
     return PolymulBatchPlan(descs, keepalive)
+
+
+# numpy mirrors of mont_request / mont_completion (48 and 16 bytes)
+def request_dtype():
+    import numpy as np
+    return np.dtype([("a", np.uint64), ("b", np.uint64), ("c", np.uint64), ("la", np.uint32), ("lb", np.uint32),
+                     ("p", np.uint32), ("reserved", np.uint32), ("id", np.uint64)])
+
+
+def completion_dtype():
+    import numpy as np
+    return np.dtype([("id", np.uint64), ("status", np.int32), ("reserved", np.int32)])
+
+
+class MontServer:
+    """Owner of a ``mont_server *`` (continuous-batching request server)."""
+
+    def __init__(self, primes, max_log2n, budget_bytes, slots=4, max_batch_coeffs=1 << 25):
+        import numpy as np
+        arr = (ctypes.c_uint32 * len(primes))(*[int(p) for p in primes])
+        h = _vp()
+        _check(lib().mont_server_create(arr, len(primes), int(max_log2n), int(budget_bytes), int(slots),
+                                        int(max_batch_coeffs), ctypes.byref(h)), "mont_server_create")
+        self._h = h
+        self._done = np.zeros(1 << 16, dtype=completion_dtype())
+
+    def submit(self, reqs, start=0, stop=None):
+        """Queue requests [start, stop) of a request_dtype() array."""
+        stop = len(reqs) if stop is None else stop
+        if stop > start:
+            ptr = reqs.ctypes.data + start * reqs.dtype.itemsize
+            _check(lib().mont_server_submit(self._h, ptr, stop - start), "mont_server_submit")
+
+    def progress(self):
+        """One non-blocking step; returns the completions (a completion_dtype() array view)."""
+        n = _sz()
+        _check(lib().mont_server_progress(self._h, self._done.ctypes.data, len(self._done), ctypes.byref(n)),
+               "mont_server_progress")
+        return self._done[:n.value]
+
+    def stats(self):
+        st = MontServerStats()
+        _check(lib().mont_server_get_stats(self._h, ctypes.byref(st)), "mont_server_get_stats")
+        return st.as_dict()
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.mont_server_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        self.close()

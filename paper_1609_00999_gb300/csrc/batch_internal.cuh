@@ -1,0 +1,69 @@
+// batch_internal.cuh -- job-list batches shared by the batch plans
+// (polymul_batch.cu) and the request server (server.cu).
+#pragma once
+#include <cstdint>
+#include <vector>
+
+#include "ntt_kernels.cuh"
+
+namespace mont {
+
+constexpr int kThreads = 256;         // threads per CTA of the persistent kernel
+constexpr int kRowLog = 12;        // row size 2^12 for split products
+constexpr int kMaxColLog = 9;      // K1 <= 9: N <= 2^21 in a batch
+constexpr int kMaxPrimes = 8;
+
+enum : uint32_t { JOB_SMALL = 0, JOB_COLF = 1, JOB_ROW = 2, JOB_COLI = 3 };
+
+struct Job {
+    uint32_t type, k, prod, idx;   // idx: tile / row index, or the number of products of a SMALL job
+};
+
+struct Prod {
+    const uint32_t *a, *b;
+    uint32_t *c;
+    uint32_t *ws;         // 2N words, large products only
+    uint32_t la, lb, lc, k;
+    uint32_t prime, k_scale;
+    uint32_t ntiles, nrows;
+};
+
+struct PrimeInfo {
+    uint32_t p, pp;
+    const uint32_t *tw, *itw;
+};
+
+struct BatchArgs {
+    const Job *jobs;
+    const Prod *prods;
+    uint32_t *sync;    // [0] job counter, [1] error word, then per product: COLF done, ROW done
+    uint32_t njobs;
+    uint32_t wait_iters;
+    unsigned long long wait_ns;
+    PrimeInfo primes[kMaxPrimes];
+};
+
+// Host-side form of a batch: the product table (scratch pointers hold word
+// offsets from the batch's scratch base until rebased) and the job list for
+// both job orders.
+struct BatchHost {
+    std::vector<Prod> prods;
+    std::vector<Job> jobs[2];
+    size_t ws_words = 0;
+};
+
+// Validates the descriptors and builds the batch.  Products are stored small
+// (N <= 2^12, sorted by size) first, then split ones.  Primes are looked up
+// in prime_list (extended, and prime_log2 raised, unless fixed_primes).
+int batch_build(const polymul_desc *descs, size_t count, BatchHost &out, std::vector<uint32_t> &prime_list,
+                std::vector<int> &prime_log2, bool fixed_primes);
+// Replaces scratch offsets by pointers into ws.
+void batch_rebase(BatchHost &b, uint32_t *ws);
+// Opts the persistent kernel into its shared memory and returns its CTAs per SM.
+int batch_occupancy(int *per_sm);
+// Resets the counters (sync_words words) and launches `grid` CTAs on jobs.
+int batch_launch(BatchArgs A, const Job *jobs, uint32_t njobs, size_t sync_words, int grid, cudaStream_t s);
+// Scratch words for one product of this output length (0 when N <= 2^12).
+size_t batch_ws_words(size_t lc);
+
+}  // namespace mont

@@ -23,45 +23,10 @@
 #include <string>
 #include <vector>
 
-#include "ntt_kernels.cuh"
+#include "batch_internal.cuh"
 
 namespace mont {
 namespace {
-
-constexpr int kThreads = 256;
-constexpr int kRowLog = 12;        // row size 2^12 for split products
-constexpr int kMaxColLog = 9;      // K1 <= 9: N <= 2^21 in a batch
-constexpr int kMaxPrimes = 8;
-
-enum : uint32_t { JOB_SMALL = 0, JOB_COLF = 1, JOB_ROW = 2, JOB_COLI = 3 };
-
-struct Job {
-    uint32_t type, k, prod, idx;   // idx: tile / row index, or the number of products of a SMALL job
-};
-
-struct Prod {
-    const uint32_t *a, *b;
-    uint32_t *c;
-    uint32_t *ws;         // 2N words, large products only
-    uint32_t la, lb, lc, k;
-    uint32_t prime, k_scale;
-    uint32_t ntiles, nrows;
-};
-
-struct PrimeInfo {
-    uint32_t p, pp;
-    const uint32_t *tw, *itw;
-};
-
-struct BatchArgs {
-    const Job *jobs;
-    const Prod *prods;
-    uint32_t *sync;    // [0] job counter, [1] error word, then per product: COLF done, ROW done
-    uint32_t njobs;
-    uint32_t wait_iters;
-    unsigned long long wait_ns;
-    PrimeInfo primes[kMaxPrimes];
-};
 
 // Column tile geometry for a 256-thread CTA: C columns of N1 = 2^K1, NT1
 // threads per column; layouts chosen (as in ntt_large.cu) for conflict-free
@@ -267,22 +232,142 @@ int teams_for(int k)
 }
 
 }  // namespace
+
+size_t batch_ws_words(size_t lc)
+{
+    const int k = ceil_log2(lc);
+    return k > kRowLog ? (size_t{2} << k) : 0;
+}
+
+int batch_build(const polymul_desc *descs, size_t count, BatchHost &out, std::vector<uint32_t> &prime_list,
+                std::vector<int> &prime_log2, bool fixed_primes)
+{
+    out.prods.clear();
+    out.jobs[0].clear();
+    out.jobs[1].clear();
+    out.ws_words = 0;
+    if (count && !descs) return MONT_EINVAL;
+    std::vector<Prod> prods(count);
+    std::vector<size_t> small, large;
+    for (size_t i = 0; i < count; i++) {
+        const polymul_desc &d = descs[i];
+        if (!d.a || !d.b || !d.c || d.la == 0 || d.lb == 0 || d.reserved != 0) return MONT_EINVAL;
+        if (d.la > (1u << 24) || d.lb > (1u << 24)) return MONT_ERANGE;
+        const size_t lc = static_cast<size_t>(d.la) + d.lb - 1;
+        const int k = ceil_log2(lc);
+        if (k > kRowLog + kMaxColLog) return MONT_EUNSUPPORTED;
+        if (any_overlap(d.c, lc * 4, d.a, size_t{d.la} * 4) || any_overlap(d.c, lc * 4, d.b, size_t{d.lb} * 4))
+            return MONT_EINVAL;
+        size_t pi = 0;
+        while (pi < prime_list.size() && prime_list[pi] != d.p) pi++;
+        if (pi == prime_list.size()) {
+            if (fixed_primes) return MONT_EINVAL;
+            if (pi == kMaxPrimes) return MONT_EUNSUPPORTED;
+            if (d.p < 3 || d.p >= 0x80000000u || !(d.p & 1u)) return MONT_EINVAL;
+            prime_list.push_back(d.p);
+            prime_log2.push_back(0);
+        }
+        if (k > prime_log2[pi]) {
+            if (fixed_primes) return MONT_ERANGE;
+            prime_log2[pi] = k;
+        }
+        Prod &P = prods[i];
+        P.a = d.a;
+        P.b = d.b;
+        P.c = d.c;
+        P.ws = nullptr;
+        P.la = d.la;
+        P.lb = d.lb;
+        P.lc = static_cast<uint32_t>(lc);
+        P.k = static_cast<uint32_t>(k);
+        P.prime = static_cast<uint32_t>(pi);
+        const uint32_t n_mod = static_cast<uint32_t>((uint64_t{1} << k) % d.p);
+        P.k_scale = host_to_mont(host_to_mont(host_powmod(n_mod, d.p - 2, d.p), d.p), d.p);   // N^-1 R^2
+        P.ntiles = P.nrows = 0;
+        if (k > kRowLog) {
+            P.ntiles = static_cast<uint32_t>(col_tiles(k - kRowLog));
+            P.nrows = 1u << (k - kRowLog);
+            P.ws = reinterpret_cast<uint32_t *>(out.ws_words);   // word offset until rebased
+            out.ws_words += size_t{2} << k;
+            large.push_back(i);
+        } else {
+            small.push_back(i);
+        }
+    }
+    std::stable_sort(small.begin(), small.end(), [&](size_t x, size_t y) { return prods[x].k < prods[y].k; });
+    out.prods.reserve(count);
+    for (size_t i : small) out.prods.push_back(prods[i]);
+    for (size_t i : large) out.prods.push_back(prods[i]);
+    const size_t nsmall = small.size();
+    std::vector<Job> colf, sm, row, coli;
+    for (size_t i = nsmall; i < count; i++) {
+        const Prod &P = out.prods[i];
+        const uint32_t id = static_cast<uint32_t>(i);
+        for (uint32_t t = 0; t < P.ntiles; t++) colf.push_back(Job{JOB_COLF, P.k, id, t});
+        for (uint32_t r = 0; r < P.nrows; r++) row.push_back(Job{JOB_ROW, P.k, id, r});
+        for (uint32_t t = 0; t < P.ntiles; t++) coli.push_back(Job{JOB_COLI, P.k, id, t});
+    }
+    for (size_t s = 0; s < nsmall;) {
+        const uint32_t k = out.prods[s].k;
+        const size_t per = static_cast<size_t>(teams_for(static_cast<int>(k)));
+        size_t e = s;
+        while (e < nsmall && e - s < per && out.prods[e].k == k) e++;
+        sm.push_back(Job{JOB_SMALL, k, static_cast<uint32_t>(s), static_cast<uint32_t>(e - s)});
+        s = e;
+    }
+    // order 0: split products' column tiles first, whole small products fill
+    // the time until their rows can start; order 1: small products first.
+    for (int order = 0; order < 2; order++) {
+        std::vector<Job> &jobs = out.jobs[order];
+        const std::vector<Job> *seq0[4] = {&colf, &sm, &row, &coli};
+        const std::vector<Job> *seq1[4] = {&sm, &colf, &row, &coli};
+        for (const std::vector<Job> *v : (order == 0 ? seq0 : seq1)) jobs.insert(jobs.end(), v->begin(), v->end());
+    }
+    return MONT_OK;
+}
+
+void batch_rebase(BatchHost &b, uint32_t *ws)
+{
+    for (Prod &P : b.prods)
+        if (P.k > static_cast<uint32_t>(kRowLog)) P.ws = ws + reinterpret_cast<size_t>(P.ws);
+}
+
+int batch_occupancy(int *per_sm)
+{
+    if (cudaFuncSetAttribute(k_polymul_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kSmemWords * sizeof(uint32_t)) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_polymul_batch, kThreads,
+                                                      kSmemWords * sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        return MONT_ECUDA;
+    }
+    return *per_sm > 0 ? MONT_OK : MONT_ECUDA;
+}
+
+int batch_launch(BatchArgs A, const Job *jobs, uint32_t njobs, size_t sync_words, int grid, cudaStream_t s)
+{
+    A.jobs = jobs;
+    A.njobs = njobs;
+    if (cudaMemsetAsync(A.sync, 0, sync_words * sizeof(uint32_t), s) != cudaSuccess) return MONT_ECUDA;
+    if (njobs == 0) return MONT_OK;
+    const unsigned g = static_cast<unsigned>(std::max(1, std::min<int>(grid, static_cast<int>(std::min<uint32_t>(njobs, 1u << 30)))));
+    k_polymul_batch<<<g, kThreads, kSmemWords * sizeof(uint32_t), s>>>(A);
+    return launch_status();
+}
+
 }  // namespace mont
 
 struct polymul_batch_plan {
     int device = 0;
-    size_t count = 0;
-    std::vector<mont::Prod> prods;       // host copy (device pointers inside)
+    mont::BatchHost host;
     std::vector<uint32_t> prime_list;
     std::vector<int> prime_log2;
     mont::BatchArgs args{};
-    std::vector<mont::Job> jobs[2];       // per job order policy
     mont::Job *d_jobs[2] = {nullptr, nullptr};
     mont::Prod *d_prods = nullptr;
     uint32_t *d_sync = nullptr;
     size_t sync_words = 0;
     uint32_t *d_ws = nullptr;
-    size_t ws_words = 0;
     int occupancy = 1;
     int sms = 1;
     polymul_batch_config cfg{};
@@ -300,44 +385,10 @@ std::map<std::string, polymul_batch_config> g_tune_cache;
 std::string signature(const polymul_batch_plan *pl)
 {
     std::map<uint32_t, size_t> hist;
-    for (const Prod &P : pl->prods) hist[P.k]++;
+    for (const Prod &P : pl->host.prods) hist[P.k]++;
     std::string s = std::to_string(pl->device) + ":";
     for (auto &kv : hist) s += std::to_string(kv.first) + "x" + std::to_string(kv.second) + ",";
     return s;
-}
-
-void build_jobs(polymul_batch_plan *pl, const std::vector<size_t> &small_order, const std::vector<size_t> &large)
-{
-    for (int order = 0; order < 2; order++) {
-        std::vector<Job> &jobs = pl->jobs[order];
-        jobs.clear();
-        std::vector<Job> colf, small, row, coli;
-        for (size_t i : large) {
-            const Prod &P = pl->prods[i];
-            for (uint32_t t = 0; t < P.ntiles; t++) colf.push_back(Job{JOB_COLF, P.k, static_cast<uint32_t>(i), t});
-            for (uint32_t r = 0; r < P.nrows; r++) row.push_back(Job{JOB_ROW, P.k, static_cast<uint32_t>(i), r});
-            for (uint32_t t = 0; t < P.ntiles; t++) coli.push_back(Job{JOB_COLI, P.k, static_cast<uint32_t>(i), t});
-        }
-        for (size_t s = 0; s < small_order.size();) {
-            const uint32_t k = pl->prods[small_order[s]].k;
-            const size_t per = static_cast<size_t>(teams_for(static_cast<int>(k)));
-            size_t e = s;
-            while (e < small_order.size() && e - s < per && pl->prods[small_order[e]].k == k) e++;
-            small.push_back(Job{JOB_SMALL, k, static_cast<uint32_t>(small_order[s]), static_cast<uint32_t>(e - s)});
-            s = e;
-        }
-        if (order == 0) {   // large products' column tiles first, small products fill the gaps
-            jobs.insert(jobs.end(), colf.begin(), colf.end());
-            jobs.insert(jobs.end(), small.begin(), small.end());
-            jobs.insert(jobs.end(), row.begin(), row.end());
-            jobs.insert(jobs.end(), coli.begin(), coli.end());
-        } else {            // small products first, large products phase by phase
-            jobs.insert(jobs.end(), small.begin(), small.end());
-            jobs.insert(jobs.end(), colf.begin(), colf.end());
-            jobs.insert(jobs.end(), row.begin(), row.end());
-            jobs.insert(jobs.end(), coli.begin(), coli.end());
-        }
-    }
 }
 
 void free_plan(polymul_batch_plan *pl)
@@ -353,16 +404,10 @@ void free_plan(polymul_batch_plan *pl)
 
 int launch(polymul_batch_plan *pl, const polymul_batch_config &cfg, cudaStream_t s)
 {
-    BatchArgs A = pl->args;
     const int order = cfg.order == 1 ? 1 : 0;
-    A.jobs = pl->d_jobs[order];
-    A.njobs = static_cast<uint32_t>(pl->jobs[order].size());
-    if (cudaMemsetAsync(pl->d_sync, 0, pl->sync_words * sizeof(uint32_t), s) != cudaSuccess) return MONT_ECUDA;
-    if (A.njobs == 0) return MONT_OK;
     const int per_sm = std::max(1, std::min(cfg.ctas_per_sm > 0 ? cfg.ctas_per_sm : pl->occupancy, pl->occupancy));
-    const size_t grid = std::min<size_t>(static_cast<size_t>(pl->sms) * per_sm, A.njobs);
-    k_polymul_batch<<<static_cast<unsigned>(grid), kThreads, kSmemWords * sizeof(uint32_t), s>>>(A);
-    return launch_status();
+    return batch_launch(pl->args, pl->d_jobs[order], static_cast<uint32_t>(pl->host.jobs[order].size()),
+                        pl->sync_words, pl->sms * per_sm, s);
 }
 
 }  // namespace
@@ -376,119 +421,35 @@ extern "C" int polymul_batch_plan_create(const polymul_desc *descs, size_t count
     if (count > (size_t{1} << 31)) return MONT_ERANGE;
     polymul_batch_plan *pl = new (std::nothrow) polymul_batch_plan();
     if (!pl) return MONT_ENOMEM;
-    if (cudaGetDevice(&pl->device) != cudaSuccess) {
-        delete pl;
-        return MONT_ECUDA;
-    }
-    pl->count = count;
-    pl->prods.resize(count);
-    std::vector<size_t> small, large;
-    size_t ws_words = 0;
-    int rc = MONT_OK;
-    for (size_t i = 0; i < count && rc == MONT_OK; i++) {
-        const polymul_desc &d = descs[i];
-        if (!d.a || !d.b || !d.c || d.la == 0 || d.lb == 0 || d.reserved != 0) rc = MONT_EINVAL;
-        else if (d.la > (1u << 24) || d.lb > (1u << 24)) rc = MONT_ERANGE;
-        if (rc != MONT_OK) break;
-        const size_t lc = static_cast<size_t>(d.la) + d.lb - 1;
-        const int k = ceil_log2(lc);
-        if (k > kRowLog + kMaxColLog) {
-            rc = MONT_EUNSUPPORTED;
-            break;
-        }
-        if (any_overlap(d.c, lc * 4, d.a, size_t{d.la} * 4) || any_overlap(d.c, lc * 4, d.b, size_t{d.lb} * 4)) {
-            rc = MONT_EINVAL;
-            break;
-        }
-        size_t pi = 0;
-        while (pi < pl->prime_list.size() && pl->prime_list[pi] != d.p) pi++;
-        if (pi == pl->prime_list.size()) {
-            if (pi == kMaxPrimes) {
-                rc = MONT_EUNSUPPORTED;
-                break;
-            }
-            pl->prime_list.push_back(d.p);
-            pl->prime_log2.push_back(0);
-        }
-        pl->prime_log2[pi] = std::max(pl->prime_log2[pi], k);
-        Prod &P = pl->prods[i];
-        P.a = d.a;
-        P.b = d.b;
-        P.c = d.c;
-        P.ws = nullptr;
-        P.la = d.la;
-        P.lb = d.lb;
-        P.lc = static_cast<uint32_t>(lc);
-        P.k = static_cast<uint32_t>(k);
-        P.prime = static_cast<uint32_t>(pi);
-        const uint32_t n_mod = static_cast<uint32_t>((uint64_t{1} << k) % d.p);
-        P.k_scale = host_to_mont(host_to_mont(host_powmod(n_mod, d.p - 2, d.p), d.p), d.p);   // N^-1 R^2
-        P.ntiles = P.nrows = 0;
-        if (k > kRowLog) {
-            P.ntiles = static_cast<uint32_t>(col_tiles(k - kRowLog));
-            P.nrows = 1u << (k - kRowLog);
-            P.ws = reinterpret_cast<uint32_t *>(ws_words);   // offset, rebased below
-            ws_words += size_t{2} << k;
-            large.push_back(i);
-        } else {
-            small.push_back(i);
-        }
-    }
-    if (rc == MONT_OK) {
-        for (size_t pi = 0; pi < pl->prime_list.size() && rc == MONT_OK; pi++) {
-            const TwTable *t = nullptr;
-            rc = get_table(pl->prime_list[pi], std::max(pl->prime_log2[pi], kRowLog), &t);
-            if (rc == MONT_OK) {
-                pl->args.primes[pi] = PrimeInfo{t->p, t->p_prime, t->fwd, t->inv};
-            }
-        }
+    int rc = cudaGetDevice(&pl->device) == cudaSuccess ? MONT_OK : MONT_ECUDA;
+    if (rc == MONT_OK) rc = batch_build(descs, count, pl->host, pl->prime_list, pl->prime_log2, false);
+    for (size_t pi = 0; pi < pl->prime_list.size() && rc == MONT_OK; pi++) {
+        const TwTable *t = nullptr;
+        rc = get_table(pl->prime_list[pi], std::max(pl->prime_log2[pi], kRowLog), &t);
+        if (rc == MONT_OK) pl->args.primes[pi] = PrimeInfo{t->p, t->p_prime, t->fwd, t->inv};
     }
     if (rc != MONT_OK) {
         delete pl;
         return rc;
     }
-    std::stable_sort(small.begin(), small.end(),
-                     [&](size_t x, size_t y) { return pl->prods[x].k < pl->prods[y].k; });
-    // SMALL jobs reference consecutive product indices: store the products
-    // in job order (small ones sorted by size, then the large ones).
-    std::vector<Prod> ordered;
-    ordered.reserve(count);
-    std::vector<size_t> small_idx, large_idx;
-    for (size_t i : small) {
-        small_idx.push_back(ordered.size());
-        ordered.push_back(pl->prods[i]);
-    }
-    for (size_t i : large) {
-        large_idx.push_back(ordered.size());
-        ordered.push_back(pl->prods[i]);
-    }
-    pl->prods.swap(ordered);
-    build_jobs(pl, small_idx, large_idx);
-
     bool ok = true;
-    pl->ws_words = ws_words;
     pl->sync_words = 2 + 2 * count;
-    ok = ok && cudaMalloc(&pl->d_sync, pl->sync_words * sizeof(uint32_t)) == cudaSuccess &&
+    ok = cudaMalloc(&pl->d_sync, pl->sync_words * sizeof(uint32_t)) == cudaSuccess &&
          cudaMemset(pl->d_sync, 0, pl->sync_words * sizeof(uint32_t)) == cudaSuccess;
-    if (ws_words) ok = ok && cudaMalloc(&pl->d_ws, ws_words * sizeof(uint32_t)) == cudaSuccess;
-    if (ok) {
-        for (Prod &P : pl->prods)
-            if (P.k > static_cast<uint32_t>(kRowLog)) P.ws = pl->d_ws + reinterpret_cast<size_t>(P.ws);
-    }
-    if (ok && count) ok = cudaMalloc(&pl->d_prods, count * sizeof(Prod)) == cudaSuccess &&
-                          cudaMemcpy(pl->d_prods, pl->prods.data(), count * sizeof(Prod), cudaMemcpyHostToDevice) ==
-                              cudaSuccess;
+    if (ok && pl->host.ws_words) ok = cudaMalloc(&pl->d_ws, pl->host.ws_words * sizeof(uint32_t)) == cudaSuccess;
+    if (ok) batch_rebase(pl->host, pl->d_ws);
+    if (ok && count)
+        ok = cudaMalloc(&pl->d_prods, count * sizeof(Prod)) == cudaSuccess &&
+             cudaMemcpy(pl->d_prods, pl->host.prods.data(), count * sizeof(Prod), cudaMemcpyHostToDevice) ==
+                 cudaSuccess;
     for (int o = 0; o < 2 && ok; o++)
-        if (!pl->jobs[o].empty())
-            ok = cudaMalloc(&pl->d_jobs[o], pl->jobs[o].size() * sizeof(Job)) == cudaSuccess &&
-                 cudaMemcpy(pl->d_jobs[o], pl->jobs[o].data(), pl->jobs[o].size() * sizeof(Job),
+        if (!pl->host.jobs[o].empty())
+            ok = cudaMalloc(&pl->d_jobs[o], pl->host.jobs[o].size() * sizeof(Job)) == cudaSuccess &&
+                 cudaMemcpy(pl->d_jobs[o], pl->host.jobs[o].data(), pl->host.jobs[o].size() * sizeof(Job),
                             cudaMemcpyHostToDevice) == cudaSuccess;
-    if (ok) ok = cudaFuncSetAttribute(k_polymul_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      kSmemWords * sizeof(uint32_t)) == cudaSuccess;
-    if (ok) ok = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pl->occupancy, k_polymul_batch, kThreads,
-                                                               kSmemWords * sizeof(uint32_t)) == cudaSuccess;
+    if (ok) ok = batch_occupancy(&pl->occupancy) == MONT_OK;
     pl->sms = device_sm_count();
-    if (!ok || pl->sms <= 0 || pl->occupancy <= 0) {
+    if (!ok || pl->sms <= 0) {
         cudaGetLastError();
         free_plan(pl);
         delete pl;
@@ -518,7 +479,7 @@ extern "C" void polymul_batch_plan_destroy(polymul_batch_plan *plan)
 
 extern "C" size_t polymul_batch_plan_workspace_bytes(const polymul_batch_plan *plan)
 {
-    return plan ? plan->ws_words * sizeof(uint32_t) : 0;
+    return plan ? plan->host.ws_words * sizeof(uint32_t) : 0;
 }
 
 extern "C" int polymul_batch_plan_get_config(const polymul_batch_plan *plan, polymul_batch_config *cfg)
@@ -641,17 +602,18 @@ extern "C" int polymul_batch_plan_tune(polymul_batch_plan *plan, cudaStream_t st
     return polymul_batch_status(plan, stream);
 }
 
-// Test hook for failure detection: makes product `index` (a split product)
-// expect one more column tile than exists, so its row jobs wait on a count
-// that is never reached; the bounded waits expire and the batch reports
+// Test hook for failure detection: makes the first split product expect one
+// more column tile than exists, so its row jobs wait on a count that is
+// never reached; the bounded waits expire and the batch reports
 // MONT_ETIMEOUT.  Undone by recreating the plan.
 extern "C" int polymul_batch_plan_inject_stall(polymul_batch_plan *plan)
 {
     if (!plan) return MONT_EINVAL;
-    for (size_t i = 0; i < plan->prods.size(); i++) {
-        if (plan->prods[i].k <= static_cast<uint32_t>(mont::kRowLog)) continue;
-        plan->prods[i].ntiles += 1;
-        if (cudaMemcpy(plan->d_prods + i, &plan->prods[i], sizeof(mont::Prod), cudaMemcpyHostToDevice) != cudaSuccess)
+    for (size_t i = 0; i < plan->host.prods.size(); i++) {
+        mont::Prod &P = plan->host.prods[i];
+        if (P.k <= static_cast<uint32_t>(mont::kRowLog)) continue;
+        P.ntiles += 1;
+        if (cudaMemcpy(plan->d_prods + i, &P, sizeof(mont::Prod), cudaMemcpyHostToDevice) != cudaSuccess)
             return MONT_ECUDA;
         return MONT_OK;
     }

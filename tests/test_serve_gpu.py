@@ -1,0 +1,88 @@
+"""The continuous-batching request server: a Poisson stream of products of
+mixed sizes and primes under a small device-memory budget.  Every result must
+be bit-exact equal to the same product computed alone (and to the oracle on
+a sample), whatever else was in flight with it."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1609_00999_gb300 import serve, synth
+
+from helpers import to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def m():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1609_00999_gb300 as m
+    from paper_1609_00999_gb300 import build
+    build.build()
+    return m
+
+
+def stream_case(n=400, lo=1 << 8, hi=1 << 15, rate=20000.0, seed=700):
+    lens = synth.loguniform_lengths(n, lo, hi, seed, 0)
+    primes = synth.choose_primes(n, seed, 1)
+    arrivals = synth.poisson_arrivals(n, rate, seed, 2)
+    wl = synth.UnevenBatch(primes, lens, lens, (seed,))
+    return wl, arrivals
+
+
+def test_stream_results_equal_alone(m):
+    import torch
+    wl, arrivals = stream_case()
+    da, db = to_dev(wl.a), to_dev(wl.b)
+    host_a = torch.from_numpy(wl.a.view(np.int32)).pin_memory()       # half the requests read host memory
+    hc = torch.full((wl.c_size,), -1, dtype=torch.int32).pin_memory()
+    n = len(wl)
+    use_host = (np.arange(n) % 2) == 1
+    a_ptrs = np.where(use_host, host_a.data_ptr(), da.data_ptr()) + 4 * wl.a_off.astype(np.int64)
+    reqs = serve.make_requests(wl.primes, wl.la, wl.lb, a_ptrs,
+                               db.data_ptr() + 4 * wl.b_off.astype(np.int64),
+                               hc.data_ptr() + 4 * wl.c_off.astype(np.int64))
+    budget = 24 << 20                                                # forces admission waits
+    server = m.MontServer(synth.PRIMES, 16, budget, slots=3, max_batch_coeffs=1 << 17)
+    lat, status, makespan = serve.run_stream(server, reqs, arrivals)
+    st = server.stats()
+    server.close()
+    assert np.all(status == m.MONT_OK)
+    assert np.all(np.isfinite(lat)) and np.all(lat >= 0)
+    assert st["completed"] == n and st["peak_bytes"] <= budget and st["batches"] > 3
+    got = hc.numpy().view(np.uint32)
+    for i in range(n):
+        ao, la = int(wl.a_off[i]), int(wl.la[i])
+        bo, lb = int(wl.b_off[i]), int(wl.lb[i])
+        co = int(wl.c_off[i])
+        alone = to_host(m.polymul(int(wl.primes[i]), da[ao:ao + la], db[bo:bo + lb]))
+        assert np.array_equal(got[co:co + la + lb - 1], alone), i
+    for i in range(0, n, 37):
+        ao, la = int(wl.a_off[i]), int(wl.la[i])
+        bo, lb = int(wl.b_off[i]), int(wl.lb[i])
+        co = int(wl.c_off[i])
+        ref = oracle.polymul_ntt(int(wl.primes[i]), wl.a[ao:ao + la], wl.b[bo:bo + lb])
+        assert np.array_equal(got[co:co + la + lb - 1], ref), i
+
+
+def test_server_rejects_bad_requests(m):
+    import torch
+    d = to_dev(np.ones(1 << 12, dtype=np.uint32))
+    out = torch.zeros(1 << 13, dtype=torch.int32, device="cuda")
+    server = m.MontServer([synth.P1], 14, 1 << 16, slots=1)
+    big = serve.make_requests([synth.P1], [4096], [4096], [d.data_ptr()], [d.data_ptr()], [out.data_ptr()])
+    with pytest.raises(m.MontError) as e:           # needs more than the whole 64 KiB budget
+        server.submit(big)
+    assert e.value.code == m.MONT_ERANGE
+    other = serve.make_requests([synth.P2], [8], [8], [d.data_ptr()], [d.data_ptr()], [out.data_ptr()])
+    with pytest.raises(m.MontError) as e:           # prime not served
+        server.submit(other)
+    assert e.value.code == m.MONT_EINVAL
+    ok = serve.make_requests([synth.P1], [100], [50], [d.data_ptr()], [d.data_ptr()], [out.data_ptr()])
+    lat, status, _ = serve.run_stream(server, ok, np.zeros(1))
+    server.close()
+    assert status[0] == m.MONT_OK
+    assert np.array_equal(to_host(out)[:149], oracle.polymul_schoolbook(synth.P1, np.ones(100, np.uint32),
+                                                                        np.ones(50, np.uint32)))
