@@ -53,6 +53,8 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--log2n", type=int, default=28, help="elements per operand (default 2^28)")
+    ap.add_argument("--sections", default="uniform,uneven,serve",
+                    help="extra polymul sections to run (comma list of uniform, uneven, serve; empty for none)")
     return ap.parse_args()
 
 
@@ -70,6 +72,14 @@ def measured_peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def measured_sm_max_mhz():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["sm_max_mhz"])
+    except Exception:
+        return 2070.0
 
 
 def source_digest(paths):
@@ -324,6 +334,24 @@ def run_gpu(args, ws, rank, local):
         cpu = {"value": 3 * 2 * n / t / 1e9, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                "sample": "one full step: 2^%d residues x 3 primes x {mont_mul, mont_fma}" % args.log2n}
 
+    extra = {}
+    if rank == 0 and ws == 1:
+        import bench_polymul as bp
+        peaks = {"hbm_gbs": measured_peaks()[0], "sm_max_mhz": measured_sm_max_mhz()}
+        secs = [x for x in args.sections.split(",") if x]
+        sampler2 = ClockSampler(bus)
+        sampler2.start()
+        if "uniform" in secs:
+            extra["polymul_uniform_4096x2048"] = bp.uniform_batch(m, torch, peaks, cpu=not args.no_cpu_baseline)
+        if "uneven" in secs:
+            extra["polymul_uneven_10000"] = bp.uneven_batch(m, torch, peaks, cpu=not args.no_cpu_baseline)
+        if "serve" in secs:
+            extra["serve_50000"] = bp.serve_stream(m, torch)
+        if secs:
+            extra["clocks_polymul_sections"] = sampler2.stop()
+        else:
+            sampler2.stop()
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
@@ -334,6 +362,7 @@ def run_gpu(args, ws, rank, local):
                            "parallelism": "replica per GPU" if ws > 1 else "single GPU"},
                 "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
                 "cpu_baseline": cpu}
+        line.update(extra)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

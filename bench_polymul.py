@@ -1,0 +1,227 @@
+"""Polynomial-multiplication sections of the benchmark (imported by bench.py).
+
+* uniform batch: 4096 products of length-2048 polynomials mod 2013265921
+  (N = 4096), one fused kernel; L2 flushed between timed launches because
+  the 64 MiB of operands fit in L2;
+* uneven batch: 10,000 products, lengths log-uniform in [2^6, 2^16], primes
+  uniform from the three Fourier primes, one persistent launch replayed from
+  a CUDA graph after autotuning, against one launch per product;
+* serve: 50,000 requests, lengths log-uniform in [2^8, 2^20], mixed primes,
+  Poisson arrivals at 0.8 x the measured saturated request rate, a 16 GB
+  device-memory budget; throughput and p50/p99 latency.
+
+Gcoef/s counts input coefficients (la + lb per product) per second.
+Integer roofline: the path runs on the two 32-bit integer pipes of each SM
+sub-partition (ALU and FMA-heavy, 16 lanes each), i.e. 128 integer lane-ops
+per SM per clock; 32x32->64 multiplies (IMAD.WIDE / IMAD.HI) issue at half
+rate and count 2.  The algorithmic lane-ops of a product are counted per
+butterfly from the method (see int_ops_polymul).
+"""
+import time
+
+import numpy as np
+
+from paper_1609_00999_gb300 import serve, synth
+
+SMS = 152
+INT_LANES_PER_SM_CLK = 128
+
+
+def int_peak_ops(sm_mhz):
+    return SMS * INT_LANES_PER_SM_CLK * sm_mhz * 1e6
+
+
+def int_ops_polymul(n, la, lb):
+    """Algorithmic integer lane-ops of one product of size n (power of two).
+
+    Non-trivial CT butterfly: REDC (wide mul 2, mul.lo 1, wide mul-add 2) +
+    conditional subtract 1 + add/subtract with their conditional subtracts 4
+    = 10; non-trivial GS butterfly: 9 (its difference feeds REDC unreduced);
+    butterfly with twiddle 1 (block 0 of every level, n - 1 per transform): 4;
+    stand-alone REDC (pointwise product, scaling of b): 6."""
+    levels = n.bit_length() - 1
+    bfly = (n // 2) * levels
+    trivial = n - 1
+    nontrivial = bfly - trivial
+    fwd = 2 * (10 * nontrivial + 4 * trivial)
+    inv = 9 * nontrivial + 4 * trivial
+    return fwd + inv + 6 * n + 6 * lb
+
+
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def uniform_batch(m, torch, peaks, steps=20, warmup=3, cpu=True):
+    import oracle
+    p, a, b = synth.batch_uniform()
+    count, L = a.shape
+    n = 1 << (2 * L - 1).bit_length()
+    da = torch.from_numpy(a.view(np.int32)).cuda()
+    db = torch.from_numpy(b.view(np.int32)).cuda()
+    out = torch.empty((count, 2 * L - 1), dtype=torch.int32, device="cuda")
+    flush = torch.empty(64 << 20, dtype=torch.int32, device="cuda")   # 256 MiB > L2
+    for _ in range(warmup):
+        m.polymul_many(p, da, db, out=out)
+    torch.cuda.synchronize()
+    # All steps are queued before one synchronize, so the GPU never waits for
+    # the host between the start event and the launch it brackets.
+    evs = []
+    for _ in range(steps):
+        flush.fill_(1)
+        e0, e1 = _events(torch)
+        e0.record()
+        m.polymul_many(p, da, db, out=out)
+        e1.record()
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    ms = float(np.mean([e0.elapsed_time(e1) for e0, e1 in evs]))
+    coeffs = count * 2 * L
+    ops = count * int_ops_polymul(n, L, L)
+    peak = int_peak_ops(peaks["sm_max_mhz"])
+    hbm_bytes = count * (2 * L + 2 * L - 1) * 4
+    res = {"workload": "4096 products, la = lb = 2048, P = 2013265921, N = 4096 (one fused kernel)",
+           "value": coeffs / ms / 1e6, "unit": "Gcoef/s", "ms": ms, "steps": steps, "warmup": warmup,
+           "l2": "flushed (256 MiB write) before every timed launch", "gpu_launches": steps,
+           "roofline": {"bound": "alu", "kernel": "k_polymul<12>", "achieved": ops / (ms / 1e3) / 1e12,
+                        "peak": peak / 1e12, "unit": "Tops/s (integer lane-ops)", "frac": ops / (ms / 1e3) / peak,
+                        "peak_source": "derived: 152 SMs x 128 int lanes/clk x %.0f MHz" % peaks["sm_max_mhz"],
+                        "algorithmic_ops": ops, "traffic": None},
+           "hbm_at_pass_count": {"passes": 1, "bytes": hbm_bytes, "achieved_gbs": hbm_bytes / (ms / 1e3) / 1e9,
+                                 "peak_gbs": peaks["hbm_gbs"],
+                                 "frac": hbm_bytes / (ms / 1e3) / 1e9 / peaks["hbm_gbs"]}}
+    # parity spot check on this run's output (full parity lives in the tests)
+    got = out[:4].cpu().numpy().view(np.uint32)
+    for i in range(4):
+        assert np.array_equal(got[i], oracle.polymul_ntt(p, a[i], b[i])), "polymul parity spot check failed"
+    if cpu:
+        off = np.arange(count, dtype=np.uint64) * L
+        lens = np.full(count, L, dtype=np.uint64)
+        t0 = time.perf_counter()
+        oracle.polymul_batch(np.full(count, p, dtype=np.uint32), a.ravel(), off, lens, b.ravel(), off, lens,
+                             np.arange(count, dtype=np.uint64) * (2 * L - 1), count * (2 * L - 1), use_ntt=True)
+        t = time.perf_counter() - t0
+        res["cpu_baseline"] = {"value": coeffs / t / 1e9, "unit": "Gcoef/s", "cores": oracle.num_threads(),
+                               "kind": "oracle", "sample": "all 4096 products (oracle radix-2 NTT, OpenMP over products)"}
+    del flush
+    return res
+
+
+def uneven_batch(m, torch, peaks, steps=10, warmup=3, cpu=True, per_product=True):
+    import oracle
+    wl = synth.batch_uneven()
+    da = torch.from_numpy(wl.a.view(np.int32)).cuda()
+    db = torch.from_numpy(wl.b.view(np.int32)).cuda()
+    dc = torch.empty(wl.c_size, dtype=torch.int32, device="cuda")
+    plan = m.PolymulBatchPlan.from_packed(wl.primes, da, wl.a_off, wl.la, db, wl.b_off, wl.lb, dc, wl.c_off)
+    t0 = time.perf_counter()
+    cfg = plan.tune(trials=2)
+    tune_s = time.perf_counter() - t0
+    for _ in range(warmup):
+        plan.run_graph()
+    torch.cuda.synchronize()
+    e0, e1 = _events(torch)
+    e0.record()
+    for _ in range(steps):
+        plan.run_graph()
+    e1.record()
+    e1.synchronize()
+    assert plan.status() == m.MONT_OK
+    ms = e0.elapsed_time(e1) / steps
+    coeffs = float((wl.la + wl.lb).sum())
+    ns = [1 << int(lc - 1).bit_length() for lc in (wl.la + wl.lb - 1)]
+    ops = float(sum(int_ops_polymul(n, int(la), int(lb)) for n, la, lb in zip(ns, wl.la, wl.lb)))
+    peak = int_peak_ops(peaks["sm_max_mhz"])
+    res = {"workload": "10,000 products, L log-uniform in [2^6, 2^16], primes uniform from "
+                       "{2013265921, 469762049, 754974721}, N padded to powers of two",
+           "value": coeffs / ms / 1e6, "unit": "Gcoef/s", "ms": ms, "steps": steps, "warmup": warmup,
+           "launch": "one persistent kernel per batch, replayed from a CUDA graph",
+           "tuned_config": {"ctas_per_sm": cfg.ctas_per_sm, "order": cfg.order}, "tune_s": tune_s,
+           "workspace_bytes": plan.workspace_bytes(), "l2": "operands + scratch (2.4 GB) larger than L2",
+           "gpu_launches": steps,
+           "roofline": {"bound": "alu", "kernel": "k_polymul_batch", "achieved": ops / (ms / 1e3) / 1e12,
+                        "peak": peak / 1e12, "unit": "Tops/s (integer lane-ops)", "frac": ops / (ms / 1e3) / peak,
+                        "algorithmic_ops": ops, "traffic": None}}
+    # spot check a few products against the oracle
+    got = dc.cpu().numpy().view(np.uint32)
+    for i in (0, 1, 9999):
+        ao, la, bo, lb, co = (int(wl.a_off[i]), int(wl.la[i]), int(wl.b_off[i]), int(wl.lb[i]), int(wl.c_off[i]))
+        ref = oracle.polymul_ntt(int(wl.primes[i]), wl.a[ao:ao + la], wl.b[bo:bo + lb])
+        assert np.array_equal(got[co:co + la + lb - 1], ref), "batch parity spot check failed"
+    if per_product:
+        L = m.lib()
+        stream = torch.cuda.current_stream().cuda_stream
+        pa, pb, pc = da.data_ptr(), db.data_ptr(), dc.data_ptr()
+        args = [(int(wl.primes[i]), pa + 4 * int(wl.a_off[i]), int(wl.la[i]), pb + 4 * int(wl.b_off[i]),
+                 int(wl.lb[i]), pc + 4 * int(wl.c_off[i])) for i in range(len(wl))]
+        for a_ in args[:50]:
+            L.polymul(a_[0], a_[1], a_[2], a_[3], a_[4], a_[5], stream)
+        torch.cuda.synchronize()
+        e0, e1 = _events(torch)
+        w0 = time.perf_counter()
+        e0.record()
+        for a_ in args:
+            rc = L.polymul(a_[0], a_[1], a_[2], a_[3], a_[4], a_[5], stream)
+            assert rc == 0
+        e1.record()
+        e1.synchronize()
+        wall = time.perf_counter() - w0
+        one_ms = e0.elapsed_time(e1)
+        res["one_launch_per_product"] = {"value": coeffs / one_ms / 1e6, "unit": "Gcoef/s", "ms": one_ms,
+                                         "host_wall_ms": wall * 1e3,
+                                         "note": "polymul() per product on one stream, same products"}
+        res["batched_over_per_product"] = one_ms / ms
+    if cpu:
+        k = 1000
+        t0 = time.perf_counter()
+        oracle.polymul_batch(wl.primes[:k], wl.a, wl.a_off[:k], wl.la[:k], wl.b, wl.b_off[:k], wl.lb[:k],
+                             wl.c_off[:k], int(wl.c_off[k - 1] + wl.la[k - 1] + wl.lb[k - 1] - 1), use_ntt=True)
+        t = time.perf_counter() - t0
+        res["cpu_baseline"] = {"value": float((wl.la[:k] + wl.lb[:k]).sum()) / t / 1e9, "unit": "Gcoef/s",
+                               "cores": oracle.num_threads(), "kind": "oracle",
+                               "sample": "first 1000 of the 10,000 products (oracle radix-2 NTT, OpenMP)"}
+    del plan
+    return res
+
+
+def serve_stream(m, torch, n=50000, budget=16 << 30, slots=4, batch_coeffs=1 << 25, load=0.8, pool_log2=24,
+                 ring_words=1 << 30):
+    lens = synth.loguniform_lengths(n, 1 << 8, 1 << 20, synth.SEED_SERVE, 0)
+    primes = synth.choose_primes(n, synth.SEED_SERVE, 1)
+    pool_n = 1 << pool_log2
+    pools = {}
+    for i, p in enumerate(synth.PRIMES):
+        pools[p] = torch.from_numpy(synth.residues(pool_n, p, synth.SEED_SERVE, 10 + i).view(np.int32)).pin_memory()
+    g = synth.rng(synth.SEED_SERVE, 3)
+    off_a = (g.random(n) * (pool_n - lens + 1)).astype(np.int64)
+    off_b = (g.random(n) * (pool_n - lens + 1)).astype(np.int64)
+    base = np.array([pools[int(p)].data_ptr() for p in primes], dtype=np.int64)
+    ring_t = torch.empty(ring_words, dtype=torch.int32).pin_memory()
+    coeffs = float(2 * lens.sum())
+
+    def make():
+        return serve.make_requests(primes, lens, lens, base + 4 * off_a, base + 4 * off_b, np.zeros(n, np.int64))
+
+    server = m.MontServer(synth.PRIMES, 21, budget, slots=slots, max_batch_coeffs=batch_coeffs)
+    # warm-up: a short closed-loop burst
+    warm = make()[:500]
+    serve.run_stream(server, warm, np.zeros(len(warm)), ring=serve.HostRing(ring_t.data_ptr(), ring_words))
+    # saturation: every request arrives at t = 0
+    lat_s, st_s, mk_s = serve.run_stream(server, make(), np.zeros(n),
+                                         ring=serve.HostRing(ring_t.data_ptr(), ring_words))
+    rate_sat = n / mk_s
+    lam = load * rate_sat
+    arrivals = synth.poisson_arrivals(n, lam, synth.SEED_SERVE, 2)
+    lat, st, mk = serve.run_stream(server, make(), arrivals, ring=serve.HostRing(ring_t.data_ptr(), ring_words))
+    stats = server.stats()
+    server.close()
+    assert np.all(st == 0) and np.all(st_s == 0), "serve: a request failed"
+    summ = serve.latency_summary(lat)
+    return {"workload": "50,000 requests, L log-uniform in [2^8, 2^20], primes uniform from the three Fourier "
+                        "primes, Poisson arrivals; operands from a seeded pinned host pool, results copied back",
+            "value": coeffs / mk / 1e9, "unit": "Gcoef/s", "requests_per_s": n / mk, "makespan_s": mk,
+            "lambda_per_s": lam, "load": load, "saturated": {"requests_per_s": rate_sat, "Gcoef_s": coeffs / mk_s / 1e9,
+                                                              **serve.latency_summary(lat_s)},
+            **summ, "budget_bytes": budget, "slots": slots, "max_batch_coeffs": batch_coeffs,
+            "batches": stats["batches"], "peak_bytes": stats["peak_bytes"],
+            "latency": "host clock, arrival (scheduled) to completion reported by mont_server_progress"}
