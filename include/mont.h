@@ -194,12 +194,13 @@ typedef struct polymul_desc {
 } polymul_desc;
 
 /* Launch shape of a batch: CTAs per SM of the persistent grid (0 = as many
- * as fit) and the job order (0: split products' column tiles first, then
+ * as fit), the job order (0: split products' column tiles first, then
  * the whole small products, then rows and output tiles; 1: small products
- * first).  Chosen by polymul_batch_plan_tune. */
+ * first) and the kernel variant.  Chosen by polymul_batch_plan_tune. */
 typedef struct polymul_batch_config {
     int ctas_per_sm;
     int order;
+    int kernel;   /* 0: registers budgeted for 2 CTAs per SM; 1: for 3 CTAs per SM */
 } polymul_batch_config;
 
 /* Library-owned plan: device copies of the job list and the product table,
@@ -228,8 +229,8 @@ int polymul_batch_run_graph(polymul_batch_plan *plan, cudaStream_t stream);
  * then incomplete; the device context stays usable). */
 int polymul_batch_status(polymul_batch_plan *plan, cudaStream_t stream);
 
-/* Autotuner: runs the batch `trials` times per launch shape (CTAs per SM x
- * job order), keeps the fastest (CUDA-event timed on `stream`) and caches it
+/* Autotuner: runs the batch `trials` times per launch shape (kernel variant
+ * x CTAs per SM x job order), keeps the fastest (CUDA-event timed on `stream`) and caches it
  * for batches with the same size histogram on this device; synchronous.
  * Returns the status of the last run. */
 int polymul_batch_plan_tune(polymul_batch_plan *plan, cudaStream_t stream, int trials);

@@ -104,10 +104,11 @@ class PolymulDesc(ctypes.Structure):
 
 class PolymulBatchConfig(ctypes.Structure):
     """Mirror of ``polymul_batch_config``."""
-    _fields_ = [("ctas_per_sm", ctypes.c_int), ("order", ctypes.c_int)]
+    _fields_ = [("ctas_per_sm", ctypes.c_int), ("order", ctypes.c_int), ("kernel", ctypes.c_int)]
 
     def __repr__(self):
-        return "PolymulBatchConfig(ctas_per_sm=%d, order=%d)" % (self.ctas_per_sm, self.order)
+        return "PolymulBatchConfig(ctas_per_sm=%d, order=%d, kernel=%d)" % (self.ctas_per_sm, self.order,
+                                                                            self.kernel)
 
 
 def _declare_batch(L):

@@ -59,10 +59,12 @@ int batch_build(const polymul_desc *descs, size_t count, BatchHost &out, std::ve
                 std::vector<int> &prime_log2, bool fixed_primes);
 // Replaces scratch offsets by pointers into ws.
 void batch_rebase(BatchHost &b, uint32_t *ws);
-// Opts the persistent kernel into its shared memory and returns its CTAs per SM.
-int batch_occupancy(int *per_sm);
+// Opts kernel variant (0: 2 CTAs/SM register budget, 1: 3 CTAs/SM) into its
+// shared memory and returns its CTAs per SM.
+int batch_occupancy(int variant, int *per_sm);
 // Resets the counters (sync_words words) and launches `grid` CTAs on jobs.
-int batch_launch(BatchArgs A, const Job *jobs, uint32_t njobs, size_t sync_words, int grid, cudaStream_t s);
+int batch_launch(BatchArgs A, const Job *jobs, uint32_t njobs, size_t sync_words, int grid, int variant,
+                 cudaStream_t s);
 // Scratch words for one product of this output length (0 when N <= 2^12).
 size_t batch_ws_words(size_t lc);
 

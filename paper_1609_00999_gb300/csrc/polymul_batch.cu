@@ -167,7 +167,11 @@ __device__ __forceinline__ void small_dispatch(uint32_t *smem, const BatchArgs &
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 2) k_polymul_batch(BatchArgs A)
+// MINB: CTAs per SM the registers are budgeted for (2: 128 registers, no
+// spills; 3: 80 registers with a few spills, more warps to hide memory
+// latency).  The autotuner picks one.
+template <int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k_polymul_batch(BatchArgs A)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ uint32_t s_job;
@@ -193,8 +197,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_polymul_batch(BatchArgs A)
             }
             __syncthreads();
             const bool ok = J.type == JOB_COLF || s_ok;
+            // Thread 0's acquire load of the counter, then the barrier, orders
+            // every thread's reads of the producers' data after their writes.
             if (ok) {
-                __threadfence();
                 if (J.type == JOB_COLF) {
                     col_job<false>(smem, P, pr, J.idx);
                 } else if (J.type == JOB_ROW) {
@@ -332,26 +337,30 @@ void batch_rebase(BatchHost &b, uint32_t *ws)
         if (P.k > static_cast<uint32_t>(kRowLog)) P.ws = ws + reinterpret_cast<size_t>(P.ws);
 }
 
-int batch_occupancy(int *per_sm)
+int batch_occupancy(int variant, int *per_sm)
 {
-    if (cudaFuncSetAttribute(k_polymul_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kSmemWords * sizeof(uint32_t)) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_polymul_batch, kThreads,
-                                                      kSmemWords * sizeof(uint32_t)) != cudaSuccess) {
+    const void *k = variant ? reinterpret_cast<const void *>(k_polymul_batch<3>)
+                            : reinterpret_cast<const void *>(k_polymul_batch<2>);
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemWords * sizeof(uint32_t)) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k, kThreads, kSmemWords * sizeof(uint32_t)) !=
+            cudaSuccess) {
         cudaGetLastError();
         return MONT_ECUDA;
     }
     return *per_sm > 0 ? MONT_OK : MONT_ECUDA;
 }
 
-int batch_launch(BatchArgs A, const Job *jobs, uint32_t njobs, size_t sync_words, int grid, cudaStream_t s)
+int batch_launch(BatchArgs A, const Job *jobs, uint32_t njobs, size_t sync_words, int grid, int variant,
+                 cudaStream_t s)
 {
     A.jobs = jobs;
     A.njobs = njobs;
     if (cudaMemsetAsync(A.sync, 0, sync_words * sizeof(uint32_t), s) != cudaSuccess) return MONT_ECUDA;
     if (njobs == 0) return MONT_OK;
     const unsigned g = static_cast<unsigned>(std::max(1, std::min<int>(grid, static_cast<int>(std::min<uint32_t>(njobs, 1u << 30)))));
-    k_polymul_batch<<<g, kThreads, kSmemWords * sizeof(uint32_t), s>>>(A);
+    if (variant) k_polymul_batch<3><<<g, kThreads, kSmemWords * sizeof(uint32_t), s>>>(A);
+    else k_polymul_batch<2><<<g, kThreads, kSmemWords * sizeof(uint32_t), s>>>(A);
     return launch_status();
 }
 
@@ -368,7 +377,8 @@ struct polymul_batch_plan {
     uint32_t *d_sync = nullptr;
     size_t sync_words = 0;
     uint32_t *d_ws = nullptr;
-    int occupancy = 1;
+    int occupancy = 1;       // CTAs per SM of the selected kernel variant
+    int occ[2] = {1, 1};     // per variant
     int sms = 1;
     polymul_batch_config cfg{};
     cudaStream_t cap_stream = nullptr;
@@ -405,9 +415,11 @@ void free_plan(polymul_batch_plan *pl)
 int launch(polymul_batch_plan *pl, const polymul_batch_config &cfg, cudaStream_t s)
 {
     const int order = cfg.order == 1 ? 1 : 0;
-    const int per_sm = std::max(1, std::min(cfg.ctas_per_sm > 0 ? cfg.ctas_per_sm : pl->occupancy, pl->occupancy));
+    const int variant = cfg.kernel == 1 ? 1 : 0;
+    const int occ = pl->occ[variant];
+    const int per_sm = std::max(1, std::min(cfg.ctas_per_sm > 0 ? cfg.ctas_per_sm : occ, occ));
     return batch_launch(pl->args, pl->d_jobs[order], static_cast<uint32_t>(pl->host.jobs[order].size()),
-                        pl->sync_words, pl->sms * per_sm, s);
+                        pl->sync_words, pl->sms * per_sm, variant, s);
 }
 
 }  // namespace
@@ -447,7 +459,8 @@ extern "C" int polymul_batch_plan_create(const polymul_desc *descs, size_t count
             ok = cudaMalloc(&pl->d_jobs[o], pl->host.jobs[o].size() * sizeof(Job)) == cudaSuccess &&
                  cudaMemcpy(pl->d_jobs[o], pl->host.jobs[o].data(), pl->host.jobs[o].size() * sizeof(Job),
                             cudaMemcpyHostToDevice) == cudaSuccess;
-    if (ok) ok = batch_occupancy(&pl->occupancy) == MONT_OK;
+    if (ok) ok = batch_occupancy(0, &pl->occ[0]) == MONT_OK && batch_occupancy(1, &pl->occ[1]) == MONT_OK;
+    pl->occupancy = pl->occ[0];
     pl->sms = device_sm_count();
     if (!ok || pl->sms <= 0) {
         cudaGetLastError();
@@ -459,8 +472,9 @@ extern "C" int polymul_batch_plan_create(const polymul_desc *descs, size_t count
     pl->args.sync = pl->d_sync;
     pl->args.wait_iters = 1u << 22;
     pl->args.wait_ns = 2000000000ull;   // 2 s per wait
-    pl->cfg.ctas_per_sm = pl->occupancy;
+    pl->cfg.ctas_per_sm = pl->occ[0];
     pl->cfg.order = 0;
+    pl->cfg.kernel = 0;
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune_cache.find(signature(pl));
@@ -491,7 +505,9 @@ extern "C" int polymul_batch_plan_get_config(const polymul_batch_plan *plan, pol
 
 extern "C" int polymul_batch_plan_set_config(polymul_batch_plan *plan, const polymul_batch_config *cfg)
 {
-    if (!plan || !cfg || cfg->ctas_per_sm < 0 || cfg->order < 0 || cfg->order > 1) return MONT_EINVAL;
+    if (!plan || !cfg || cfg->ctas_per_sm < 0 || cfg->order < 0 || cfg->order > 1 || cfg->kernel < 0 ||
+        cfg->kernel > 1)
+        return MONT_EINVAL;
     plan->cfg = *cfg;
     return MONT_OK;
 }
@@ -523,7 +539,8 @@ extern "C" int polymul_batch_run_graph(polymul_batch_plan *plan, cudaStream_t st
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return MONT_ECUDA;
     if (dev != plan->device) return MONT_EINVAL;
-    if (plan->graph && (plan->graph_cfg.ctas_per_sm != plan->cfg.ctas_per_sm || plan->graph_cfg.order != plan->cfg.order)) {
+    if (plan->graph && (plan->graph_cfg.ctas_per_sm != plan->cfg.ctas_per_sm || plan->graph_cfg.order != plan->cfg.order ||
+                        plan->graph_cfg.kernel != plan->cfg.kernel)) {
         cudaGraphExecDestroy(plan->graph);
         plan->graph = nullptr;
     }
@@ -561,7 +578,7 @@ extern "C" int polymul_batch_status(polymul_batch_plan *plan, cudaStream_t strea
     return err ? MONT_ETIMEOUT : MONT_OK;
 }
 
-// Autotuner: times every (CTAs per SM, job order) choice `trials` times
+// Autotuner: times every (kernel variant, CTAs per SM, job order) choice `trials` times
 // with CUDA events on `stream` and keeps the fastest; the result is cached
 // for batches with the same size histogram on this device.
 extern "C" int polymul_batch_plan_tune(polymul_batch_plan *plan, cudaStream_t stream, int trials)
@@ -572,11 +589,13 @@ extern "C" int polymul_batch_plan_tune(polymul_batch_plan *plan, cudaStream_t st
     polymul_batch_config best = plan->cfg;
     float best_ms = 1e30f;
     int rc = MONT_OK;
-    for (int per = 1; per <= plan->occupancy && rc == MONT_OK; per++)
+    for (int variant = 0; variant < 2 && rc == MONT_OK; variant++)
+    for (int per = 1; per <= plan->occ[variant] && rc == MONT_OK; per++)
         for (int order = 0; order < 2 && rc == MONT_OK; order++) {
             polymul_batch_config c{};
             c.ctas_per_sm = per;
             c.order = order;
+            c.kernel = variant;
             rc = mont::launch(plan, c, stream);   // warm-up
             float total = 0.f;
             for (int t = 0; t < trials && rc == MONT_OK; t++) {

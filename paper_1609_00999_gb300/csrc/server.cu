@@ -245,7 +245,7 @@ int launch_slot(mont_server *sv, Slot &s)
         A.prods = s.d_prods;
         A.sync = s.d_sync;
         rc = batch_launch(A, s.d_jobs, static_cast<uint32_t>(s.host.jobs[0].size()), 2 + 2 * s.host.prods.size(),
-                          sv->sms * sv->occupancy, s.stream);
+                          sv->sms * sv->occupancy, 1, s.stream);
     }
     if (rc == MONT_OK) {
         for (const Req &q : s.reqs) {
@@ -313,7 +313,7 @@ extern "C" int mont_server_create(const uint32_t *primes, int nprimes, uint32_t 
             sv->args.primes[i] = PrimeInfo{t->p, t->p_prime, t->fwd, t->inv};
         }
     }
-    if (rc == MONT_OK) rc = batch_occupancy(&sv->occupancy);
+    if (rc == MONT_OK) rc = batch_occupancy(1, &sv->occupancy);   // 3-CTA/SM variant: fastest on mixed sizes
     sv->sms = device_sm_count();
     if (rc == MONT_OK && sv->sms <= 0) rc = MONT_ECUDA;
     if (rc == MONT_OK && cudaMalloc(&sv->arena_base, budget_bytes) != cudaSuccess) rc = MONT_ENOMEM;
