@@ -171,10 +171,12 @@ _U32_DTYPES = (torch.int32,) + ((torch.uint32,) if hasattr(torch, "uint32") else
 
 
 def _dev_ptr(t, name):
+    """Address of a CUDA tensor, or of a pinned host tensor (the kernels then
+    read and write it in place over the CPU-GPU link, with no staging copy)."""
     if not isinstance(t, torch.Tensor):
         raise TypeError("%s must be a torch tensor" % name)
-    if not t.is_cuda:
-        raise ValueError("%s must be a CUDA tensor" % name)
+    if not t.is_cuda and not t.is_pinned():
+        raise ValueError("%s must be a CUDA tensor or a pinned host tensor" % name)
     if t.dtype not in _U32_DTYPES:
         raise TypeError("%s must be int32 or uint32 (got %s)" % (name, t.dtype))
     if not t.is_contiguous():
@@ -184,6 +186,8 @@ def _dev_ptr(t, name):
 
 def _stream_handle(stream, device):
     if stream is None:
+        if device is None or getattr(device, "type", "cuda") != "cuda":
+            return torch.cuda.current_stream().cuda_stream
         return torch.cuda.current_stream(device).cuda_stream
     if isinstance(stream, torch.cuda.Stream):
         return stream.cuda_stream

@@ -137,3 +137,25 @@ def test_full_size_elementwise(m, prime_index):
     assert np.array_equal(to_host(out), oracle.mont_fma(p, a, b, c))
     del da, db, dc, out
     torch.cuda.empty_cache()
+
+
+def test_pinned_host_operands_zero_copy(m):
+    """Kernels on pinned host buffers (read/written in place over the CPU-GPU
+    link) give the same results as on device buffers."""
+    import torch
+    p, n = synth.P1, (1 << 20) + 5
+    a = synth.residues(n, p, 204, 0)
+    b = synth.residues(n, p, 204, 1)
+    c = synth.residues(n, p, 204, 2)
+    ctx = m.mont_setup(p)
+    ha, hb, hc = (torch.from_numpy(x.view(np.int32)).pin_memory() for x in (a, b, c))
+    ho = torch.empty(n, dtype=torch.int32).pin_memory()
+    m.mont_mul(ctx, ha, hb, out=ho)
+    torch.cuda.synchronize()
+    assert np.array_equal(ho.numpy().view(np.uint32), oracle.mont_mul(p, a, b))
+    m.mont_fma(ctx, ha, hb, hc, out=ho)
+    torch.cuda.synchronize()
+    assert np.array_equal(ho.numpy().view(np.uint32), oracle.mont_fma(p, a, b, c))
+    dout = torch.empty(n, dtype=torch.int32, device="cuda")
+    m.mont_mul(ctx, ha, to_dev(b), out=dout)                   # host and device operands mixed
+    assert np.array_equal(to_host(dout), oracle.mont_mul(p, a, b))
