@@ -83,6 +83,25 @@ int mont_mul(const mont_ctx *ctx, const uint32_t *a, const uint32_t *b, uint32_t
 int mont_fma(const mont_ctx *ctx, const uint32_t *a, const uint32_t *b, const uint32_t *c,
              uint32_t *out, size_t n, cudaStream_t stream);
 
+/*
+ * out[i] = a[i] b[i] mod p on plain residues by Barrett reduction (Alg. 1):
+ * k = ceil(log2 p), P' = floor(2^(2k) / p), m = floor(ab / 2^k),
+ * q = floor(m P' / 2^k), t = ab - qP, subtract P while t >= P (at most 3
+ * times).  p odd, 3 <= p < 2^31, else MONT_EINVAL.
+ */
+int barrett_mulmod(uint32_t p, const uint32_t *a, const uint32_t *b, uint32_t *out, size_t n,
+                   cudaStream_t stream);
+
+/*
+ * out[i] = a[i] b[i] R^-1 mod P (the value REDC returns) by Montgomery
+ * reduction over a Fourier prime P = c 2^n + 1 (Alg. 3): multiplies by c 2^n
+ * replace the multiply by P', and sign masks replace the compare.  Needs
+ * 2n >= 32 and, for the 31-bit sign tests to hold, P < 2^30 (so not
+ * 2013265921); otherwise MONT_ERANGE.
+ */
+int fourier_redc_mul(const mont_ctx *ctx, const uint32_t *a, const uint32_t *b, uint32_t *out, size_t n,
+                     cudaStream_t stream);
+
 /* ------------------------------------------------------------------------
  * Number-theoretic transform and polynomial multiplication.
  *

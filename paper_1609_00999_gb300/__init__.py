@@ -13,3 +13,4 @@ from ._binding import mont_release_workspaces, polymul_many_ws, polymul_noalloc,
 from ._binding import (PolymulBatchConfig, PolymulBatchPlan, PolymulDesc,  # noqa: F401
                        polymul_batch_plan_create)
 from ._binding import MontServer, MontServerStats, completion_dtype, request_dtype  # noqa: F401
+from ._binding import barrett_mulmod, fourier_redc_mul  # noqa: F401

@@ -67,7 +67,10 @@ def _declare(L):
     L.from_mont.argtypes = [ctxp, _vp, _vp, _sz, _vp]
     L.mont_mul.argtypes = [ctxp, _vp, _vp, _vp, _sz, _vp]
     L.mont_fma.argtypes = [ctxp, _vp, _vp, _vp, _vp, _sz, _vp]
-    for name in ("mont_setup", "to_mont", "from_mont", "mont_mul", "mont_fma"):
+    L.barrett_mulmod.argtypes = [ctypes.c_uint32, _vp, _vp, _vp, _sz, _vp]
+    L.fourier_redc_mul.argtypes = [ctxp, _vp, _vp, _vp, _sz, _vp]
+    for name in ("mont_setup", "to_mont", "from_mont", "mont_mul", "mont_fma", "barrett_mulmod",
+                 "fourier_redc_mul"):
         getattr(L, name).restype = ctypes.c_int
     _declare_ntt(L)
 
@@ -250,6 +253,27 @@ def mont_fma(ctx, a, b, c, out=None, stream=None):
     out = _out_like(a, out)
     _check(lib().mont_fma(ctypes.byref(ctx), _dev_ptr(a, "a"), _dev_ptr(b, "b"), _dev_ptr(c, "c"),
                           _dev_ptr(out, "out"), a.numel(), _stream_handle(stream, a.device)), "mont_fma")
+    return out
+
+
+def barrett_mulmod(p, a, b, out=None, stream=None):
+    """out = a b mod p on plain residues (Barrett reduction, Alg. 1)."""
+    if a.numel() != b.numel():
+        raise ValueError("a and b differ in size")
+    out = _out_like(a, out)
+    _check(lib().barrett_mulmod(int(p), _dev_ptr(a, "a"), _dev_ptr(b, "b"), _dev_ptr(out, "out"), a.numel(),
+                                _stream_handle(stream, a.device)), "barrett_mulmod")
+    return out
+
+
+def fourier_redc_mul(ctx, a, b, out=None, stream=None):
+    """out = a b R^-1 mod P by Montgomery reduction over a Fourier prime (Alg. 3; P < 2^30)."""
+    ctx = _ctx(ctx)
+    if a.numel() != b.numel():
+        raise ValueError("a and b differ in size")
+    out = _out_like(a, out)
+    _check(lib().fourier_redc_mul(ctypes.byref(ctx), _dev_ptr(a, "a"), _dev_ptr(b, "b"), _dev_ptr(out, "out"),
+                                  a.numel(), _stream_handle(stream, a.device)), "fourier_redc_mul")
     return out
 
 

@@ -1,4 +1,6 @@
-// elementwise.cu -- to_mont / from_mont / mont_mul / mont_fma over vectors.
+// elementwise.cu -- to_mont / from_mont / mont_mul / mont_fma over vectors, and
+// the two other reductions of Sec. 3.1 (Barrett, Alg. 1; Montgomery over
+// Fourier primes, Alg. 3) as elementwise kernels.
 //
 // The data-parallel REDC of Sec. 3.2 on sm_103a: each thread is a lane, each
 // thread moves 128-bit (uint4) vectors with coalesced loads, and a grid-stride
@@ -12,28 +14,70 @@
 namespace mont {
 namespace {
 
-enum Op { OP_SCALE = 0, OP_MUL = 1, OP_FMA = 2 };
+enum Op { OP_SCALE = 0, OP_MUL = 1, OP_FMA = 2, OP_BARRETT = 3, OP_FOURIER = 4 };
+
+// Per-launch constants: the modulus, P', and for OP_SCALE the multiplier k;
+// for OP_BARRETT k = ceil(log2 P) and aux = floor(2^(2k) / P); for OP_FOURIER
+// aux = c 2^n = P - 1.
+struct EwParams {
+    uint32_t p, pp, k, aux;
+};
+
+// Alg. 1 (Barrett): m = floor(ab / 2^k), q = floor(m P' / 2^k), t = ab - qP,
+// then subtract P while t >= P (at most three times, t < 4P).  64-bit
+// intermediates: ab < 2^62, m P' < 2^63, t < 4P < 2^33.
+__device__ __forceinline__ uint32_t barrett(uint32_t a, uint32_t b, uint32_t p, uint32_t k, uint32_t pb)
+{
+    const uint64_t T = static_cast<uint64_t>(a) * b;
+    const uint64_t m = T >> k;
+    const uint64_t q = (m * pb) >> k;
+    uint64_t t = T - q * p;
+#pragma unroll
+    for (int i = 0; i < 3; i++) t = t >= p ? t - p : t;
+    return static_cast<uint32_t>(t);
+}
+
+// Alg. 3 (Montgomery over the Fourier prime P = c 2^n + 1, R = 2^32, 2n >= 32):
+// q1 = ab / R, r1 = ab mod R, (q2, r2) = (c 2^n r1) / R, mod R,
+// q3 = (c 2^n r2) / R, t = q1 - q2 + q3 in (-(P-1), 2(P-1)), then the
+// sign-mask corrections.  The 31-bit sign tests need 2(P-1) < 2^31, i.e.
+// P < 2^30 (the host rejects larger P).  Result: ab R^-1 mod P, as REDC.
+__device__ __forceinline__ uint32_t fourier_redc(uint32_t a, uint32_t b, uint32_t p, uint32_t w)
+{
+    const uint64_t T = static_cast<uint64_t>(a) * b;
+    const uint32_t q1 = static_cast<uint32_t>(T >> 32), r1 = static_cast<uint32_t>(T);
+    const uint64_t U = static_cast<uint64_t>(r1) * w;
+    const uint32_t q2 = static_cast<uint32_t>(U >> 32), r2 = static_cast<uint32_t>(U);
+    const uint32_t q3 = __umulhi(r2, w);
+    int32_t t = static_cast<int32_t>(q1 - q2 + q3);
+    t += (t >> 31) & static_cast<int32_t>(p);
+    t -= static_cast<int32_t>(p);
+    t += (t >> 31) & static_cast<int32_t>(p);
+    return static_cast<uint32_t>(t);
+}
 
 constexpr int kThreads = 256;
 constexpr int kIlp = 2;
 
 template <int OP>
-__device__ __forceinline__ uint32_t apply(uint32_t a, uint32_t b, uint32_t c, uint32_t p, uint32_t pp)
+__device__ __forceinline__ uint32_t apply(uint32_t a, uint32_t b, uint32_t c, const EwParams &q)
 {
     // OP_SCALE: b is the launch-wide constant k (R^2 mod P for to_mont, 1 for from_mont).
-    const uint32_t t = mont_mul(a, b, p, pp);
-    if constexpr (OP == OP_FMA) return add_mod(t, c, p);
+    if constexpr (OP == OP_BARRETT) return barrett(a, b, q.p, q.k, q.aux);
+    if constexpr (OP == OP_FOURIER) return fourier_redc(a, b, q.p, q.aux);
+    const uint32_t t = mont_mul(a, b, q.p, q.pp);
+    if constexpr (OP == OP_FMA) return add_mod(t, c, q.p);
     return t;
 }
 
 template <int OP>
-__device__ __forceinline__ uint4 apply4(uint4 a, uint4 b, uint4 c, uint32_t p, uint32_t pp)
+__device__ __forceinline__ uint4 apply4(uint4 a, uint4 b, uint4 c, const EwParams &q)
 {
     uint4 r;
-    r.x = apply<OP>(a.x, b.x, c.x, p, pp);
-    r.y = apply<OP>(a.y, b.y, c.y, p, pp);
-    r.z = apply<OP>(a.z, b.z, c.z, p, pp);
-    r.w = apply<OP>(a.w, b.w, c.w, p, pp);
+    r.x = apply<OP>(a.x, b.x, c.x, q);
+    r.y = apply<OP>(a.y, b.y, c.y, q);
+    r.z = apply<OP>(a.z, b.z, c.z, q);
+    r.w = apply<OP>(a.w, b.w, c.w, q);
     return r;
 }
 
@@ -42,13 +86,13 @@ __device__ __forceinline__ uint4 apply4(uint4 a, uint4 b, uint4 c, uint32_t p, u
 template <int OP>
 __global__ void __launch_bounds__(kThreads)
 k_elementwise(const uint32_t *__restrict__ a, const uint32_t *__restrict__ b,
-              const uint32_t *__restrict__ c, uint32_t *__restrict__ out, size_t n4, uint32_t tail,
-              uint32_t p, uint32_t pp, uint32_t k)
+              const uint32_t *__restrict__ c, uint32_t *__restrict__ out, size_t n4, uint32_t tail, EwParams q)
 {
     const uint4 *a4 = reinterpret_cast<const uint4 *>(a);
     const uint4 *b4 = reinterpret_cast<const uint4 *>(b);
     const uint4 *c4 = reinterpret_cast<const uint4 *>(c);
     uint4 *o4 = reinterpret_cast<uint4 *>(out);
+    const uint32_t k = q.k;
     const uint4 kk = make_uint4(k, k, k, k);
     const uint4 zero = make_uint4(0, 0, 0, 0);
     const size_t stride = static_cast<size_t>(gridDim.x) * kThreads;
@@ -63,19 +107,19 @@ k_elementwise(const uint32_t *__restrict__ a, const uint32_t *__restrict__ b,
             vc[u] = OP == OP_FMA ? __ldcs(c4 + i + u * stride) : zero;
         }
 #pragma unroll
-        for (int u = 0; u < kIlp; u++) __stcs(o4 + i + u * stride, apply4<OP>(va[u], vb[u], vc[u], p, pp));
+        for (int u = 0; u < kIlp; u++) __stcs(o4 + i + u * stride, apply4<OP>(va[u], vb[u], vc[u], q));
     }
     for (; i < n4; i += stride) {
         const uint4 va = __ldcs(a4 + i);
         const uint4 vb = OP == OP_SCALE ? kk : __ldcs(b4 + i);
         const uint4 vc = OP == OP_FMA ? __ldcs(c4 + i) : zero;
-        __stcs(o4 + i, apply4<OP>(va, vb, vc, p, pp));
+        __stcs(o4 + i, apply4<OP>(va, vb, vc, q));
     }
     if (blockIdx.x == 0 && threadIdx.x < tail) {
         const size_t j = 4 * n4 + threadIdx.x;
         const uint32_t vb = OP == OP_SCALE ? k : b[j];
         const uint32_t vc = OP == OP_FMA ? c[j] : 0u;
-        out[j] = apply<OP>(a[j], vb, vc, p, pp);
+        out[j] = apply<OP>(a[j], vb, vc, q);
     }
 }
 
@@ -83,14 +127,13 @@ k_elementwise(const uint32_t *__restrict__ a, const uint32_t *__restrict__ b,
 template <int OP>
 __global__ void __launch_bounds__(kThreads)
 k_elementwise_scalar(const uint32_t *__restrict__ a, const uint32_t *__restrict__ b,
-                     const uint32_t *__restrict__ c, uint32_t *__restrict__ out, size_t n, uint32_t p,
-                     uint32_t pp, uint32_t k)
+                     const uint32_t *__restrict__ c, uint32_t *__restrict__ out, size_t n, EwParams q)
 {
     const size_t stride = static_cast<size_t>(gridDim.x) * kThreads;
     for (size_t i = static_cast<size_t>(blockIdx.x) * kThreads + threadIdx.x; i < n; i += stride) {
-        const uint32_t vb = OP == OP_SCALE ? k : b[i];
+        const uint32_t vb = OP == OP_SCALE ? q.k : b[i];
         const uint32_t vc = OP == OP_FMA ? c[i] : 0u;
-        out[i] = apply<OP>(a[i], vb, vc, p, pp);
+        out[i] = apply<OP>(a[i], vb, vc, q);
     }
 }
 
@@ -100,11 +143,9 @@ inline bool aligned16(const void *q)
 }
 
 template <int OP>
-int launch(const mont_ctx *ctx, const uint32_t *a, const uint32_t *b, const uint32_t *c, uint32_t *out,
-           size_t n, uint32_t k, cudaStream_t stream)
+int launch(const EwParams &q, const uint32_t *a, const uint32_t *b, const uint32_t *c, uint32_t *out, size_t n,
+           cudaStream_t stream)
 {
-    int rc = check_ctx(ctx);
-    if (rc != MONT_OK) return rc;
     if (n == 0) return MONT_OK;
     if (!a || !out || (OP != OP_SCALE && !b) || (OP == OP_FMA && !c)) return MONT_EINVAL;
     if (n > (SIZE_MAX >> 3)) return MONT_ERANGE;
@@ -122,14 +163,22 @@ int launch(const mont_ctx *ctx, const uint32_t *a, const uint32_t *b, const uint
         const size_t n4 = n / 4;
         const size_t want = (n4 + kThreads - 1) / kThreads;
         const unsigned grid = static_cast<unsigned>(want < 1 ? 1 : (want < max_blocks ? want : max_blocks));
-        k_elementwise<OP><<<grid, kThreads, 0, stream>>>(a, b, c, out, n4, static_cast<uint32_t>(n & 3),
-                                                         ctx->p, ctx->p_prime, k);
+        k_elementwise<OP><<<grid, kThreads, 0, stream>>>(a, b, c, out, n4, static_cast<uint32_t>(n & 3), q);
     } else {
         const size_t want = (n + kThreads - 1) / kThreads;
         const unsigned grid = static_cast<unsigned>(want < max_blocks ? want : max_blocks);
-        k_elementwise_scalar<OP><<<grid, kThreads, 0, stream>>>(a, b, c, out, n, ctx->p, ctx->p_prime, k);
+        k_elementwise_scalar<OP><<<grid, kThreads, 0, stream>>>(a, b, c, out, n, q);
     }
     return launch_status();
+}
+
+template <int OP>
+int launch_ctx(const mont_ctx *ctx, const uint32_t *a, const uint32_t *b, const uint32_t *c, uint32_t *out,
+               size_t n, uint32_t k, cudaStream_t stream)
+{
+    const int rc = check_ctx(ctx);
+    if (rc != MONT_OK) return rc;
+    return launch<OP>(EwParams{ctx->p, ctx->p_prime, k, 0u}, a, b, c, out, n, stream);
 }
 
 }  // namespace
@@ -138,23 +187,47 @@ int launch(const mont_ctx *ctx, const uint32_t *a, const uint32_t *b, const uint
 extern "C" int to_mont(const mont_ctx *ctx, const uint32_t *in, uint32_t *out, size_t n, cudaStream_t stream)
 {
     if (!ctx) return MONT_EINVAL;
-    return mont::launch<mont::OP_SCALE>(ctx, in, nullptr, nullptr, out, n, ctx->r2_mod_p, stream);
+    return mont::launch_ctx<mont::OP_SCALE>(ctx, in, nullptr, nullptr, out, n, ctx->r2_mod_p, stream);
 }
 
 extern "C" int from_mont(const mont_ctx *ctx, const uint32_t *in, uint32_t *out, size_t n,
                          cudaStream_t stream)
 {
-    return mont::launch<mont::OP_SCALE>(ctx, in, nullptr, nullptr, out, n, 1u, stream);
+    return mont::launch_ctx<mont::OP_SCALE>(ctx, in, nullptr, nullptr, out, n, 1u, stream);
 }
 
 extern "C" int mont_mul(const mont_ctx *ctx, const uint32_t *a, const uint32_t *b, uint32_t *out, size_t n,
                         cudaStream_t stream)
 {
-    return mont::launch<mont::OP_MUL>(ctx, a, b, nullptr, out, n, 0u, stream);
+    return mont::launch_ctx<mont::OP_MUL>(ctx, a, b, nullptr, out, n, 0u, stream);
 }
 
 extern "C" int mont_fma(const mont_ctx *ctx, const uint32_t *a, const uint32_t *b, const uint32_t *c,
                         uint32_t *out, size_t n, cudaStream_t stream)
 {
-    return mont::launch<mont::OP_FMA>(ctx, a, b, c, out, n, 0u, stream);
+    return mont::launch_ctx<mont::OP_FMA>(ctx, a, b, c, out, n, 0u, stream);
+}
+
+extern "C" int barrett_mulmod(uint32_t p, const uint32_t *a, const uint32_t *b, uint32_t *out, size_t n,
+                              cudaStream_t stream)
+{
+    if (p < 3 || !(p & 1u) || p >= 0x80000000u) return MONT_EINVAL;
+    uint32_t k = 0;
+    while ((uint64_t{1} << k) < p) k++;                                // k = ceil(log2 P)
+    const uint64_t pb = (uint64_t{1} << (2 * k)) / p;                   // P' = floor(2^(2k) / P) < 2^32
+    return mont::launch<mont::OP_BARRETT>(mont::EwParams{p, 0u, k, static_cast<uint32_t>(pb)}, a, b, nullptr, out,
+                                          n, stream);
+}
+
+extern "C" int fourier_redc_mul(const mont_ctx *ctx, const uint32_t *a, const uint32_t *b, uint32_t *out, size_t n,
+                                cudaStream_t stream)
+{
+    const int rc = mont::check_ctx(ctx);
+    if (rc != MONT_OK) return rc;
+    const uint32_t w = ctx->p - 1;                                     // c 2^n
+    uint32_t n2 = 0;
+    while (!((w >> n2) & 1u)) n2++;
+    if (2 * n2 < 32 || ctx->p >= (1u << 30)) return MONT_ERANGE;      // Fourier prime with 2n >= 32, P < 2^30
+    return mont::launch<mont::OP_FOURIER>(mont::EwParams{ctx->p, ctx->p_prime, 0u, w}, a, b, nullptr, out, n,
+                                          stream);
 }
