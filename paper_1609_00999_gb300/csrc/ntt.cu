@@ -49,7 +49,7 @@ k_polymul(PolyArgs A)
     const uint32_t *ga = A.a + (valid ? prod * A.la : 0);
     const uint32_t *gb = A.b + (valid ? prod * A.lb : 0);
     uint32_t *gc = A.c + (valid ? prod * A.lc : 0);
-    uint32_t *sm = smem + static_cast<size_t>(team) * 2 * (1 << LOGN);
+    uint32_t *sm = smem + static_cast<size_t>(team) * team_smem_words<LOGN>();
     polymul_team<LOGN, true, true>(sm, tid, ga, valid ? A.la : 0, gb, valid ? A.lb : 0, gc, valid ? A.lc : 0,
                                    A.tw, A.itw, 0, 0, A.p, A.pp, A.k_scale);
 }
@@ -74,7 +74,7 @@ k_ntt_fwd(NttArgs A)
     const size_t prod = static_cast<size_t>(blockIdx.x) * teams_of<LOGN>() + team;
     const bool valid = prod < A.batch;
     uint32_t *g = A.data + (valid ? prod * N : 0);
-    const SwzLayout lay[1] = {{smem + static_cast<size_t>(team) * N}};
+    const PadLayout lay[1] = {{smem + static_cast<size_t>(team) * PadLayout::words(N)}};
     for (int k = tid; k < N; k += NT) lay[0][k] = valid ? g[k] : 0u;
     __syncthreads();
     fwd_passes<LOGN, NT, 1, true, 0, NP - 1>(lay, tid, A.tw, 0, 0, Mod{A.p, A.pp});
@@ -94,7 +94,7 @@ k_ntt_inv(NttArgs A)
     const size_t prod = static_cast<size_t>(blockIdx.x) * teams_of<LOGN>() + team;
     const bool valid = prod < A.batch;
     uint32_t *g = A.data + (valid ? prod * N : 0);
-    const SwzLayout lay = {smem + static_cast<size_t>(team) * N};
+    const PadLayout lay = {smem + static_cast<size_t>(team) * PadLayout::words(N)};
     for (int k = tid; k < N; k += NT) lay[A.bitrev ? k : brev<LOGN>(k)] = valid ? g[k] : 0u;
     __syncthreads();
     inv_passes<LOGN, NT, true, NP - 1, 0>(lay, tid, A.tw, 0, 0, Mod{A.p, A.pp});
@@ -106,7 +106,7 @@ template <int LOGN>
 int launch_polymul_smem(const PolyArgs &A, cudaStream_t s)
 {
     constexpr int T = teams_of<LOGN>(), NT = nt_of<LOGN>();
-    const size_t smem = static_cast<size_t>(T) * 2 * (size_t{1} << LOGN) * sizeof(uint32_t);
+    const size_t smem = static_cast<size_t>(T) * team_smem_words<LOGN>() * sizeof(uint32_t);
     if (ensure_smem(k_polymul<LOGN>, smem) != MONT_OK) return MONT_ECUDA;
     const size_t grid = (A.count + T - 1) / T;
     if (grid > 0x7FFFFFFFu) return MONT_ERANGE;
@@ -118,7 +118,7 @@ template <int LOGN>
 int launch_ntt_smem(const NttArgs &A, bool inverse, cudaStream_t s)
 {
     constexpr int T = teams_of<LOGN>(), NT = nt_of<LOGN>();
-    const size_t smem = static_cast<size_t>(T) * (size_t{1} << LOGN) * sizeof(uint32_t);
+    const size_t smem = static_cast<size_t>(T) * PadLayout::words(1 << LOGN) * sizeof(uint32_t);
     const size_t grid = (A.batch + T - 1) / T;
     if (grid > 0x7FFFFFFFu) return MONT_ERANGE;
     if (inverse) {

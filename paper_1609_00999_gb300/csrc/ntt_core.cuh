@@ -195,8 +195,33 @@ struct PassGeom {
 // Whole transform in one buffer with the XOR swizzle.
 struct SwzLayout {
     uint32_t *base;
+    static constexpr bool kAdditive = false;
     __device__ __forceinline__ uint32_t &operator[](int j) const { return base[swz(j)]; }
 };
+
+// Whole transform in one buffer with one padding word after every 32:
+// word(j) = j + (j >> 5).  For j = base + t*HMIN with base and t*HMIN on
+// disjoint bits (true for every group of every pass), word(j) =
+// word(base) + word(t*HMIN), so each element of a group is addressed as a
+// per-group pointer plus a compile-time offset, with no index arithmetic.
+// Banks: the strided group accesses are at most 2-way conflicted.
+struct PadLayout {
+    uint32_t *base;
+    static constexpr bool kAdditive = true;
+    static constexpr int words(int n) { return n + (n >> 5); }
+    __host__ __device__ static constexpr int off(int j) { return j + (j >> 5); }
+    __device__ __forceinline__ uint32_t &operator[](int j) const { return base[off(j)]; }
+    __device__ __forceinline__ uint32_t *at(int j) const { return base + off(j); }
+};
+
+// Element base + k of a layout (k a compile-time offset after unrolling,
+// on bits disjoint from base).
+template <class L>
+__device__ __forceinline__ uint32_t &elem(const L &lay, int base, int k)
+{
+    if constexpr (L::kAdditive) return lay.at(base)[L::off(k)];
+    else return lay[base + k];
+}
 
 // Column c of a column tile: base = c * (N1 + PAD), XOR of the low five bits
 // with XR = (c * MUL) & 31, optionally on top of swz.  Chosen per column size
@@ -206,6 +231,7 @@ template <bool SW>
 struct ColLayout {
     uint32_t *base;
     int xr;
+    static constexpr bool kAdditive = false;
     __device__ __forceinline__ uint32_t &operator[](int j) const { return base[(SW ? swz(j) : j) ^ xr]; }
 };
 
@@ -231,10 +257,10 @@ __device__ __forceinline__ void fwd_pass(const L (&lay)[NARR], int tid, const ui
             const int base = PG::base(tid, r), blk = PG::blk(tid, r);
             uint32_t x[1][PG::G];
 #pragma unroll
-            for (int t = 0; t < PG::G; t++) x[0][t] = lay[a][base + t * PG::HMIN];
+            for (int t = 0; t < PG::G; t++) x[0][t] = elem(lay[a], base, t * PG::HMIN);
             ct_group<PG::E, 1, BASE0 && PG::S0 == 0>(x, tw, s_base + PG::S0, (b << PG::S0) + blk, m);
 #pragma unroll
-            for (int t = 0; t < PG::G; t++) lay[a][base + t * PG::HMIN] = x[0][t];
+            for (int t = 0; t < PG::G; t++) elem(lay[a], base, t * PG::HMIN) = x[0][t];
         }
 }
 
@@ -248,10 +274,10 @@ __device__ __forceinline__ void inv_pass(const L &lay, int tid, const uint32_t *
         const int base = PG::base(tid, r), blk = PG::blk(tid, r);
         uint32_t x[1][PG::G];
 #pragma unroll
-        for (int t = 0; t < PG::G; t++) x[0][t] = lay[base + t * PG::HMIN];
+        for (int t = 0; t < PG::G; t++) x[0][t] = elem(lay, base, t * PG::HMIN);
         gs_group<PG::E, 1, BASE0 && PG::S0 == 0>(x, itw, s_base + PG::S0, (b << PG::S0) + blk, m);
 #pragma unroll
-        for (int t = 0; t < PG::G; t++) lay[base + t * PG::HMIN] = x[0][t];
+        for (int t = 0; t < PG::G; t++) elem(lay, base, t * PG::HMIN) = x[0][t];
     }
 }
 
@@ -292,8 +318,8 @@ __device__ __forceinline__ void fused_middle_pass(const L (&lay)[2], int tid, co
         uint32_t x[2][PL::G];
 #pragma unroll
         for (int t = 0; t < PL::G; t++) {
-            x[0][t] = lay[0][base + t * PL::HMIN];
-            x[1][t] = lay[1][base + t * PL::HMIN];
+            x[0][t] = elem(lay[0], base, t * PL::HMIN);
+            x[1][t] = elem(lay[1], base, t * PL::HMIN);
         }
         ct_group<PL::E, 2, BASE0 && PL::S0 == 0>(x, tw, s_base + PL::S0, blk, m);
         uint32_t y[1][PL::G];
@@ -301,7 +327,7 @@ __device__ __forceinline__ void fused_middle_pass(const L (&lay)[2], int tid, co
         for (int t = 0; t < PL::G; t++) y[0][t] = mont_mul(x[0][t], x[1][t], m.p, m.pp);
         gs_group<PL::E, 1, BASE0 && PL::S0 == 0>(y, itw, s_base + PL::S0, blk, m);
 #pragma unroll
-        for (int t = 0; t < PL::G; t++) lay[0][base + t * PL::HMIN] = y[0][t];
+        for (int t = 0; t < PL::G; t++) elem(lay[0], base, t * PL::HMIN) = y[0][t];
     }
 }
 

@@ -32,6 +32,14 @@ constexpr int min_ctas_of()
     return teams_of<LOGN>() * nt_of<LOGN>() <= 256 ? 3 : 1;
 }
 
+// Shared-memory words one team needs for a product of 2^LOGN (both operands,
+// padded layout).
+template <int LOGN>
+constexpr int team_smem_words()
+{
+    return 2 * PadLayout::words(1 << LOGN);
+}
+
 struct PolyArgs {
     const uint32_t *a, *b;
     uint32_t *c;
@@ -52,7 +60,7 @@ int ensure_smem(K kernel, size_t bytes)
 }
 
 // One product (or one row block of a product) by one team of nt_of<LOGN>()
-// threads with 2 * 2^LOGN words of shared memory at sm:
+// threads with team_smem_words<LOGN>() words of shared memory at sm:
 // c[0 .. lc) = inverse( forward(a) * forward(b * scale) ), where the
 // sub-transform is block b_idx of the levels s_base .. s_base + LOGN - 1 of
 // the whole transform (s_base = 0, b_idx = 0 for a complete product).
@@ -73,7 +81,7 @@ __device__ __forceinline__ void polymul_team(uint32_t *sm, int tid, const uint32
             gc[0] = mont_mul(ga[0], bb, p, pp);
         }
     } else {
-        const SwzLayout lay[2] = {{sm}, {sm + N}};
+        const PadLayout lay[2] = {{sm}, {sm + PadLayout::words(N)}};
         using P0 = PassGeom<LOGN, NT, 0>;
         const int la32 = static_cast<int>(la), lb32 = static_cast<int>(lb), lc32 = static_cast<int>(lc);
         if constexpr (NP == 1) {
@@ -116,7 +124,7 @@ __device__ __forceinline__ void polymul_team(uint32_t *sm, int tid, const uint32
                     }
                     ct_group<P0::E, 1, BASE0>(x, tw, s_base, b_idx, md);
 #pragma unroll
-                    for (int t = 0; t < P0::G; t++) lay[a][base + t * P0::HMIN] = x[0][t];
+                    for (int t = 0; t < P0::G; t++) elem(lay[a], base, t * P0::HMIN) = x[0][t];
                 }
             }
         }
@@ -131,7 +139,7 @@ __device__ __forceinline__ void polymul_team(uint32_t *sm, int tid, const uint32
                 const int base = P0::base(tid, r);
                 uint32_t y[1][P0::G];
 #pragma unroll
-                for (int t = 0; t < P0::G; t++) y[0][t] = lay[0][base + t * P0::HMIN];
+                for (int t = 0; t < P0::G; t++) y[0][t] = elem(lay[0], base, t * P0::HMIN);
                 gs_group<P0::E, 1, BASE0>(y, itw, s_base, b_idx, md);
 #pragma unroll
                 for (int t = 0; t < P0::G; t++) {

@@ -129,7 +129,7 @@ k_row_ntt(RowNttArgs A, size_t prod0)
     const size_t prod = prod0 + blockIdx.y;
     const int r = blockIdx.x;
     uint32_t *g = A.data + prod * A.n + (static_cast<size_t>(r) << K2);
-    const SwzLayout lay[1] = {{smem}};
+    const PadLayout lay[1] = {{smem}};
     for (int k = threadIdx.x; k < N2; k += NT) lay[0][k] = g[k];
     __syncthreads();
     if constexpr (!INVERSE) fwd_passes<K2, NT, 1, false, 0, NP - 1>(lay, threadIdx.x, A.tw, A.k1, r, Mod{A.p, A.pp});
@@ -175,7 +175,7 @@ int launch_col(const ColArgs &A, size_t nops, size_t count, cudaStream_t s)
 template <int K2>
 int launch_row_polymul(const RowArgs &A, size_t count, cudaStream_t s)
 {
-    const size_t smem = 2 * (size_t{1} << K2) * sizeof(uint32_t);
+    const size_t smem = team_smem_words<K2>() * sizeof(uint32_t);
     if (ensure_smem(k_row_polymul<K2>, smem) != MONT_OK) return MONT_ECUDA;
     const unsigned rows = static_cast<unsigned>(A.n >> K2);
     for (size_t first = 0; first < count; first += kMaxGridZ) {
@@ -189,7 +189,7 @@ int launch_row_polymul(const RowArgs &A, size_t count, cudaStream_t s)
 template <int K2, bool INVERSE>
 int launch_row_ntt(const RowNttArgs &A, size_t count, cudaStream_t s)
 {
-    const size_t smem = (size_t{1} << K2) * sizeof(uint32_t);
+    const size_t smem = PadLayout::words(1 << K2) * sizeof(uint32_t);
     if (ensure_smem(k_row_ntt<K2, INVERSE>, smem) != MONT_OK) return MONT_ECUDA;
     const unsigned rows = static_cast<unsigned>(A.n >> K2);
     for (size_t first = 0; first < count; first += kMaxGridZ) {

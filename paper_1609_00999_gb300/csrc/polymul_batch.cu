@@ -43,7 +43,7 @@ struct Col256 {
     static constexpr int WORDS = C * STRIDE;
 };
 
-constexpr int kSmemWords = 2 * 4352 > 2 * (1 << kRowLog) ? 2 * 4352 : 2 * (1 << kRowLog);
+constexpr int kSmemWords = 2 * 4352 > team_smem_words<kRowLog>() ? 2 * 4352 : team_smem_words<kRowLog>();
 
 __device__ __forceinline__ unsigned long long globaltimer()
 {
@@ -142,8 +142,8 @@ __device__ __forceinline__ void small_job(uint32_t *smem, const BatchArgs &A, co
     const bool valid = static_cast<uint32_t>(team) < J.idx;
     const Prod &P = A.prods[J.prod + (valid ? team : 0)];
     const PrimeInfo &pr = A.primes[P.prime];
-    static_assert(T * 2 * N <= kSmemWords, "small job does not fit");
-    polymul_team<K, true, true>(smem + team * 2 * N, tid, P.a, valid ? P.la : 0, P.b, valid ? P.lb : 0, P.c,
+    static_assert(T * team_smem_words<K>() <= kSmemWords, "small job does not fit");
+    polymul_team<K, true, true>(smem + team * team_smem_words<K>(), tid, P.a, valid ? P.la : 0, P.b, valid ? P.lb : 0, P.c,
                                 valid ? P.lc : 0, pr.tw, pr.itw, 0, 0, pr.p, pr.pp, P.k_scale);
 }
 

@@ -84,7 +84,7 @@ void fill_table(std::vector<uint32_t> &t, uint32_t p, uint32_t g, int log2max, b
 int get_table(uint32_t p, int log2n, const TwTable **out)
 {
     if (p >= 0x80000000u || p < 3 || !(p & 1u)) return MONT_EINVAL;
-    if (log2n < 0 || log2n > kMaxLog2N || log2n > two_adicity(p)) return MONT_ERANGE;
+    if (log2n < 0 || log2n > kMaxLog2N) return MONT_ERANGE;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return MONT_ECUDA;
     std::lock_guard<std::mutex> lock(g_mu);
@@ -96,6 +96,7 @@ int get_table(uint32_t p, int log2n, const TwTable **out)
             return MONT_OK;
         }
     if (!is_prime32(p)) return MONT_EINVAL;
+    if (log2n > two_adicity(p)) return MONT_ERANGE;
     // Build at least 2^12 entries so small sizes share one table.
     int lg = log2n < 12 ? 12 : log2n;
     if (lg > two_adicity(p)) lg = two_adicity(p);
