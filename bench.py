@@ -55,6 +55,8 @@ def parse_args():
     ap.add_argument("--log2n", type=int, default=28, help="elements per operand (default 2^28)")
     ap.add_argument("--sections", default="uniform,uneven,serve",
                     help="extra polymul sections to run (comma list of uniform, uneven, serve; empty for none)")
+    ap.add_argument("--no-per-product", action="store_true",
+                    help="skip the one-launch-per-product comparison of the uneven batch")
     return ap.parse_args()
 
 
@@ -63,6 +65,17 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def max_over_ranks(value, dist=None, device=None):
+    """Largest value over all ranks (the contract's timing rule); identity
+    without a process group.  Works with nccl (device tensor) and gloo (CPU)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device or "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def measured_peaks():
@@ -265,11 +278,7 @@ def run_gpu(args, ws, rank, local):
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop()
-    elapsed_ms = t0.elapsed_time(t1)
-    if dist is not None:
-        tt = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(tt.item())
+    elapsed_ms = max_over_ranks(t0.elapsed_time(t1), dist, "cuda")
     launches = args.steps * len(dev) * len(OPS)
     per_op_ms = {op: [e0.elapsed_time(e1) for e0, e1 in events[op]] for op in OPS}
     mulmods = args.steps * len(dev) * len(OPS) * n * ws
@@ -320,11 +329,7 @@ def run_gpu(args, ws, rank, local):
             e2e_step()
         torch.cuda.synchronize()
         barrier()
-        e2e_s = time.perf_counter() - w0
-        if dist is not None:
-            tt = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_s = float(tt.item())
+        e2e_s = max_over_ranks(time.perf_counter() - w0, dist, "cuda")
         e2e = {"value": args.e2e_steps * len(dev) * len(OPS) * n * ws / e2e_s / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": len(dev) * (8 + 12) * n, "d2h_bytes_per_step": len(dev) * (4 + 4) * n,
                "steps": args.e2e_steps,
@@ -349,7 +354,8 @@ def run_gpu(args, ws, rank, local):
         if "uniform" in secs:
             extra["polymul_uniform_4096x2048"] = bp.uniform_batch(m, torch, peaks, cpu=not args.no_cpu_baseline)
         if "uneven" in secs:
-            extra["polymul_uneven_10000"] = bp.uneven_batch(m, torch, peaks, cpu=not args.no_cpu_baseline)
+            extra["polymul_uneven_10000"] = bp.uneven_batch(m, torch, peaks, cpu=not args.no_cpu_baseline,
+                                                            per_product=not args.no_per_product)
         if "serve" in secs:
             extra["serve_50000"] = bp.serve_stream(m, torch)
         if secs:
