@@ -215,7 +215,9 @@ typedef struct polymul_desc {
 /* Launch shape of a batch: CTAs per SM of the persistent grid (0 = as many
  * as fit), the job order (0: split products' column tiles first, then
  * the whole small products, then rows and output tiles; 1: small products
- * first) and the kernel variant.  Chosen by polymul_batch_plan_tune. */
+ * first; 2, 3: software-pipelined, rows of one product run beside the column
+ * tiles of a later one, lag 32 or 64 products) and the kernel variant.
+ * Chosen by polymul_batch_plan_tune. */
 typedef struct polymul_batch_config {
     int ctas_per_sm;
     int order;

@@ -43,12 +43,20 @@ struct BatchArgs {
     PrimeInfo primes[kMaxPrimes];
 };
 
+// Job orders: 0 = split products' column tiles, then whole small products,
+// then rows, then output tiles; 1 = small products first; 2 and 3 =
+// software-pipelined: rows of product i follow the column tiles of product
+// i + D and the output tiles of product i - D, with the small products spread
+// evenly in between (D = 32 and 64), so memory-heavy tile jobs and
+// compute-heavy row jobs run at the same time.
+constexpr int kJobOrders = 4;
+
 // Host-side form of a batch: the product table (scratch pointers hold word
 // offsets from the batch's scratch base until rebased) and the job list for
-// both job orders.
+// every job order.
 struct BatchHost {
     std::vector<Prod> prods;
-    std::vector<Job> jobs[2];
+    std::vector<Job> jobs[kJobOrders];
     size_t ws_words = 0;
 };
 

@@ -248,8 +248,7 @@ int batch_build(const polymul_desc *descs, size_t count, BatchHost &out, std::ve
                 std::vector<int> &prime_log2, bool fixed_primes)
 {
     out.prods.clear();
-    out.jobs[0].clear();
-    out.jobs[1].clear();
+    for (auto &j : out.jobs) j.clear();
     out.ws_words = 0;
     if (count && !descs) return MONT_EINVAL;
     std::vector<Prod> prods(count);
@@ -328,6 +327,32 @@ int batch_build(const polymul_desc *descs, size_t count, BatchHost &out, std::ve
         const std::vector<Job> *seq1[4] = {&sm, &colf, &row, &coli};
         for (const std::vector<Job> *v : (order == 0 ? seq0 : seq1)) jobs.insert(jobs.end(), v->begin(), v->end());
     }
+    // orders 2, 3: rounds r = 0, 1, ...: column tiles of split product r, rows
+    // of product r - D, output tiles of product r - 2D, and an even share of
+    // the small products.  Every job waits only on jobs of earlier rounds.
+    const size_t nlarge = count - nsmall;
+    std::vector<size_t> colf_at(nlarge + 1, 0), row_at(nlarge + 1, 0);
+    for (size_t i = 0; i < nlarge; i++) {
+        colf_at[i + 1] = colf_at[i] + out.prods[nsmall + i].ntiles;
+        row_at[i + 1] = row_at[i] + out.prods[nsmall + i].nrows;
+    }
+    for (int order = 2; order < kJobOrders; order++) {
+        const size_t D = order == 2 ? 32 : 64;
+        std::vector<Job> &jobs = out.jobs[order];
+        jobs.reserve(colf.size() + sm.size() + row.size() + coli.size());
+        const size_t rounds = nlarge + 2 * D;
+        size_t si = 0;
+        for (size_t r = 0; r < rounds; r++) {
+            if (r < nlarge) jobs.insert(jobs.end(), colf.begin() + colf_at[r], colf.begin() + colf_at[r + 1]);
+            if (r >= D && r - D < nlarge)
+                jobs.insert(jobs.end(), row.begin() + row_at[r - D], row.begin() + row_at[r - D + 1]);
+            if (r >= 2 * D && r - 2 * D < nlarge)
+                jobs.insert(jobs.end(), coli.begin() + colf_at[r - 2 * D], coli.begin() + colf_at[r - 2 * D + 1]);
+            const size_t until = sm.size() * (r + 1) / rounds;
+            for (; si < until; si++) jobs.push_back(sm[si]);
+        }
+        for (; si < sm.size(); si++) jobs.push_back(sm[si]);
+    }
     return MONT_OK;
 }
 
@@ -372,7 +397,7 @@ struct polymul_batch_plan {
     std::vector<uint32_t> prime_list;
     std::vector<int> prime_log2;
     mont::BatchArgs args{};
-    mont::Job *d_jobs[2] = {nullptr, nullptr};
+    mont::Job *d_jobs[mont::kJobOrders] = {};
     mont::Prod *d_prods = nullptr;
     uint32_t *d_sync = nullptr;
     size_t sync_words = 0;
@@ -405,8 +430,7 @@ void free_plan(polymul_batch_plan *pl)
 {
     if (pl->graph) cudaGraphExecDestroy(pl->graph);
     if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
-    cudaFree(pl->d_jobs[0]);
-    cudaFree(pl->d_jobs[1]);
+    for (mont::Job *j : pl->d_jobs) cudaFree(j);
     cudaFree(pl->d_prods);
     cudaFree(pl->d_sync);
     cudaFree(pl->d_ws);
@@ -414,7 +438,7 @@ void free_plan(polymul_batch_plan *pl)
 
 int launch(polymul_batch_plan *pl, const polymul_batch_config &cfg, cudaStream_t s)
 {
-    const int order = cfg.order == 1 ? 1 : 0;
+    const int order = (cfg.order >= 0 && cfg.order < kJobOrders) ? cfg.order : 0;
     const int variant = cfg.kernel == 1 ? 1 : 0;
     const int occ = pl->occ[variant];
     const int per_sm = std::max(1, std::min(cfg.ctas_per_sm > 0 ? cfg.ctas_per_sm : occ, occ));
@@ -454,7 +478,7 @@ extern "C" int polymul_batch_plan_create(const polymul_desc *descs, size_t count
         ok = cudaMalloc(&pl->d_prods, count * sizeof(Prod)) == cudaSuccess &&
              cudaMemcpy(pl->d_prods, pl->host.prods.data(), count * sizeof(Prod), cudaMemcpyHostToDevice) ==
                  cudaSuccess;
-    for (int o = 0; o < 2 && ok; o++)
+    for (int o = 0; o < kJobOrders && ok; o++)
         if (!pl->host.jobs[o].empty())
             ok = cudaMalloc(&pl->d_jobs[o], pl->host.jobs[o].size() * sizeof(Job)) == cudaSuccess &&
                  cudaMemcpy(pl->d_jobs[o], pl->host.jobs[o].data(), pl->host.jobs[o].size() * sizeof(Job),
@@ -505,7 +529,7 @@ extern "C" int polymul_batch_plan_get_config(const polymul_batch_plan *plan, pol
 
 extern "C" int polymul_batch_plan_set_config(polymul_batch_plan *plan, const polymul_batch_config *cfg)
 {
-    if (!plan || !cfg || cfg->ctas_per_sm < 0 || cfg->order < 0 || cfg->order > 1 || cfg->kernel < 0 ||
+    if (!plan || !cfg || cfg->ctas_per_sm < 0 || cfg->order < 0 || cfg->order >= mont::kJobOrders || cfg->kernel < 0 ||
         cfg->kernel > 1)
         return MONT_EINVAL;
     plan->cfg = *cfg;
@@ -591,7 +615,7 @@ extern "C" int polymul_batch_plan_tune(polymul_batch_plan *plan, cudaStream_t st
     int rc = MONT_OK;
     for (int variant = 0; variant < 2 && rc == MONT_OK; variant++)
     for (int per = 1; per <= plan->occ[variant] && rc == MONT_OK; per++)
-        for (int order = 0; order < 2 && rc == MONT_OK; order++) {
+        for (int order = 0; order < mont::kJobOrders && rc == MONT_OK; order++) {
             polymul_batch_config c{};
             c.ctas_per_sm = per;
             c.order = order;

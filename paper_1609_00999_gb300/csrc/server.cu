@@ -27,6 +27,7 @@ namespace mont {
 namespace {
 
 constexpr size_t kAlign = 256;
+constexpr int kServeOrder = 2;   // software-pipelined job order (lag 32 products)
 
 // First-fit allocator over one device region, offsets in bytes.
 class Arena {
@@ -223,7 +224,7 @@ int launch_slot(mont_server *sv, Slot &s)
         for (const Req &q : s.reqs) ws_of[q.dc] = q.dws;
         for (Prod &P : s.host.prods)
             if (P.k > static_cast<uint32_t>(kRowLog)) P.ws = ws_of[P.c];
-        rc = grow_slot(s, s.host.jobs[0].size(), s.host.prods.size());
+        rc = grow_slot(s, s.host.jobs[kServeOrder].size(), s.host.prods.size());
     }
     if (rc == MONT_OK) {
         for (const Req &q : s.reqs) {
@@ -231,10 +232,10 @@ int launch_slot(mont_server *sv, Slot &s)
                 cudaMemcpyAsync(q.db, q.r.b, size_t{q.r.lb} * 4, cudaMemcpyDefault, s.stream) != cudaSuccess)
                 rc = MONT_ECUDA;
         }
-        std::copy(s.host.jobs[0].begin(), s.host.jobs[0].end(), s.h_jobs);
+        std::copy(s.host.jobs[kServeOrder].begin(), s.host.jobs[kServeOrder].end(), s.h_jobs);
         std::copy(s.host.prods.begin(), s.host.prods.end(), s.h_prods);
         if (rc == MONT_OK &&
-            (cudaMemcpyAsync(s.d_jobs, s.h_jobs, s.host.jobs[0].size() * sizeof(Job), cudaMemcpyHostToDevice,
+            (cudaMemcpyAsync(s.d_jobs, s.h_jobs, s.host.jobs[kServeOrder].size() * sizeof(Job), cudaMemcpyHostToDevice,
                              s.stream) != cudaSuccess ||
              cudaMemcpyAsync(s.d_prods, s.h_prods, s.host.prods.size() * sizeof(Prod), cudaMemcpyHostToDevice,
                              s.stream) != cudaSuccess))
@@ -244,7 +245,7 @@ int launch_slot(mont_server *sv, Slot &s)
         BatchArgs A = sv->args;
         A.prods = s.d_prods;
         A.sync = s.d_sync;
-        rc = batch_launch(A, s.d_jobs, static_cast<uint32_t>(s.host.jobs[0].size()), 2 + 2 * s.host.prods.size(),
+        rc = batch_launch(A, s.d_jobs, static_cast<uint32_t>(s.host.jobs[kServeOrder].size()), 2 + 2 * s.host.prods.size(),
                           sv->sms * sv->occupancy, 1, s.stream);
     }
     if (rc == MONT_OK) {

@@ -70,9 +70,9 @@ def test_graph_replay_and_tuning_give_identical_results(m):
     assert plan.status() == m.MONT_OK
     assert np.array_equal(to_host(dc)[:wl.c_size], ref)
     cfg = plan.tune(trials=1)
-    assert cfg.ctas_per_sm >= 1 and cfg.order in (0, 1)
-    for order in (0, 1):
-        c = m.PolymulBatchConfig(1, order)
+    assert cfg.ctas_per_sm >= 1 and cfg.order in (0, 1, 2, 3) and cfg.kernel in (0, 1)
+    for order, kernel in ((0, 0), (1, 1), (2, 0), (3, 1)):
+        c = m.PolymulBatchConfig(1 + kernel, order, kernel)
         plan.config = c
         dc.fill_(-1)
         plan.run_graph()
