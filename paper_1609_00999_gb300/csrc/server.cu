@@ -16,7 +16,9 @@
 // memory frees up and launched on the next idle slot, so their work overlaps
 // with the batches already on the device.  Twiddle tables for the server's
 // primes are built once and stay resident; the device job and product tables
-// of each slot are reused across batches.
+// of each slot are reused across batches.  Small requests' copies are one
+// copy-kernel launch per direction and batch; large ones use the copy
+// engines.
 #include <deque>
 #include <map>
 #include <vector>
@@ -73,6 +75,38 @@ private:
     size_t used_ = 0, total_ = 0;
 };
 
+// One contiguous copy of n words (either side host or device memory: the
+// copy kernel reads and writes through unified addresses).
+struct CopyDesc {
+    const uint32_t *src;
+    uint32_t *dst;
+    uint64_t n;
+};
+
+// Requests with at most this many input coefficients have their operands
+// and results moved by the copy kernel (one launch per direction and batch);
+// larger ones use the copy engines (one cudaMemcpyAsync per buffer).  Most
+// requests are small but most bytes are in the large ones, so this removes
+// most per-copy host calls while the bulk still streams on the copy engines.
+constexpr uint64_t kKernelCopyMax = uint64_t{1} << 16;
+
+// Many small copies in one launch: CTA i takes descriptors i, i + grid, ...
+__global__ void __launch_bounds__(256) k_copy_many(const CopyDesc *__restrict__ d, uint32_t count)
+{
+    for (uint32_t i = blockIdx.x; i < count; i += gridDim.x) {
+        const CopyDesc c = d[i];
+        uint64_t j = threadIdx.x;
+        for (; j + 3 * 256 < c.n; j += 4 * 256) {
+            const uint32_t v0 = c.src[j], v1 = c.src[j + 256], v2 = c.src[j + 512], v3 = c.src[j + 768];
+            c.dst[j] = v0;
+            c.dst[j + 256] = v1;
+            c.dst[j + 512] = v2;
+            c.dst[j + 768] = v3;
+        }
+        for (; j < c.n; j += 256) c.dst[j] = c.src[j];
+    }
+}
+
 struct Req {
     mont_request r;
     size_t off = 0, bytes = 0;   // arena region: a | b | c | scratch
@@ -91,6 +125,9 @@ struct Slot {
     Job *h_jobs = nullptr;     // pinned staging
     Prod *h_prods = nullptr;
     uint32_t *h_err = nullptr;
+    CopyDesc *d_copy = nullptr, *h_copy = nullptr;
+    size_t cap_copy = 0;
+    std::vector<CopyDesc> copies;
     BatchHost host;
 };
 
@@ -119,6 +156,22 @@ struct mont_server {
 
 namespace mont {
 namespace {
+
+int grow_copies(Slot &s, size_t n)
+{
+    if (n <= s.cap_copy) return MONT_OK;
+    const size_t cap = std::max(n, 2 * s.cap_copy);
+    cudaFree(s.d_copy);
+    cudaFreeHost(s.h_copy);
+    s.d_copy = nullptr;
+    s.h_copy = nullptr;
+    s.cap_copy = 0;
+    if (cudaMalloc(&s.d_copy, cap * sizeof(CopyDesc)) != cudaSuccess ||
+        cudaMallocHost(&s.h_copy, cap * sizeof(CopyDesc)) != cudaSuccess)
+        return MONT_ENOMEM;
+    s.cap_copy = cap;
+    return MONT_OK;
+}
 
 int grow_slot(Slot &s, size_t njobs, size_t nprods)
 {
@@ -226,20 +279,46 @@ int launch_slot(mont_server *sv, Slot &s)
             if (P.k > static_cast<uint32_t>(kRowLog)) P.ws = ws_of[P.c];
         rc = grow_slot(s, s.host.jobs[kServeOrder].size(), s.host.prods.size());
     }
+    // Small requests' copies as descriptor lists for the copy kernel: operands
+    // first [0, ngather), results after.
+    size_t ngather = 0;
+    if (rc == MONT_OK) {
+        s.copies.clear();
+        for (const Req &q : s.reqs)
+            if (uint64_t{q.r.la} + q.r.lb <= kKernelCopyMax) {
+                s.copies.push_back(CopyDesc{q.r.a, q.da, q.r.la});
+                s.copies.push_back(CopyDesc{q.r.b, q.db, q.r.lb});
+            }
+        ngather = s.copies.size();
+        for (const Req &q : s.reqs)
+            if (uint64_t{q.r.la} + q.r.lb <= kKernelCopyMax)
+                s.copies.push_back(CopyDesc{q.dc, q.r.c, static_cast<uint64_t>(q.r.la) + q.r.lb - 1});
+        rc = grow_copies(s, s.copies.size());
+    }
     if (rc == MONT_OK) {
         for (const Req &q : s.reqs) {
+            if (uint64_t{q.r.la} + q.r.lb <= kKernelCopyMax) continue;
             if (cudaMemcpyAsync(q.da, q.r.a, size_t{q.r.la} * 4, cudaMemcpyDefault, s.stream) != cudaSuccess ||
                 cudaMemcpyAsync(q.db, q.r.b, size_t{q.r.lb} * 4, cudaMemcpyDefault, s.stream) != cudaSuccess)
                 rc = MONT_ECUDA;
         }
+        std::copy(s.copies.begin(), s.copies.end(), s.h_copy);
         std::copy(s.host.jobs[kServeOrder].begin(), s.host.jobs[kServeOrder].end(), s.h_jobs);
         std::copy(s.host.prods.begin(), s.host.prods.end(), s.h_prods);
         if (rc == MONT_OK &&
-            (cudaMemcpyAsync(s.d_jobs, s.h_jobs, s.host.jobs[kServeOrder].size() * sizeof(Job), cudaMemcpyHostToDevice,
+            ((!s.copies.empty() && cudaMemcpyAsync(s.d_copy, s.h_copy, s.copies.size() * sizeof(CopyDesc),
+                                                   cudaMemcpyHostToDevice, s.stream) != cudaSuccess) ||
+             cudaMemcpyAsync(s.d_jobs, s.h_jobs, s.host.jobs[kServeOrder].size() * sizeof(Job), cudaMemcpyHostToDevice,
                              s.stream) != cudaSuccess ||
              cudaMemcpyAsync(s.d_prods, s.h_prods, s.host.prods.size() * sizeof(Prod), cudaMemcpyHostToDevice,
                              s.stream) != cudaSuccess))
             rc = MONT_ECUDA;
+    }
+    const size_t copy_grid = static_cast<size_t>(sv->sms) * 4;
+    if (rc == MONT_OK && ngather) {
+        k_copy_many<<<static_cast<unsigned>(std::min(copy_grid, ngather)), 256, 0, s.stream>>>(
+            s.d_copy, static_cast<uint32_t>(ngather));
+        rc = launch_status();
     }
     if (rc == MONT_OK) {
         BatchArgs A = sv->args;
@@ -249,7 +328,14 @@ int launch_slot(mont_server *sv, Slot &s)
                           sv->sms * sv->occupancy, 1, s.stream);
     }
     if (rc == MONT_OK) {
+        const size_t nscatter = s.copies.size() - ngather;
+        if (nscatter) {
+            k_copy_many<<<static_cast<unsigned>(std::min(copy_grid, nscatter)), 256, 0, s.stream>>>(
+                s.d_copy + ngather, static_cast<uint32_t>(nscatter));
+            rc = launch_status();
+        }
         for (const Req &q : s.reqs) {
+            if (uint64_t{q.r.la} + q.r.lb <= kKernelCopyMax) continue;
             const size_t lc = static_cast<size_t>(q.r.la) + q.r.lb - 1;
             if (cudaMemcpyAsync(q.r.c, q.dc, lc * 4, cudaMemcpyDefault, s.stream) != cudaSuccess) rc = MONT_ECUDA;
         }
@@ -284,6 +370,8 @@ void destroy_server(mont_server *sv)
         cudaFreeHost(s.h_jobs);
         cudaFreeHost(s.h_prods);
         cudaFreeHost(s.h_err);
+        cudaFree(s.d_copy);
+        cudaFreeHost(s.h_copy);
         if (s.done) cudaEventDestroy(s.done);
         if (s.stream) cudaStreamDestroy(s.stream);
     }
