@@ -266,7 +266,9 @@ int polymul_batch_plan_set_wait_limit(polymul_batch_plan *plan, uint32_t iterati
 int polymul_batch_plan_inject_stall(polymul_batch_plan *plan);
 
 /* ------------------------------------------------------------------------
- * Continuous-batching request server (single host thread, one device).
+ * Continuous-batching request server (one device).  The caller drives it
+ * from one host thread; internally one launcher thread per slot builds and
+ * queues its batches.
  * ------------------------------------------------------------------------ */
 
 /* One request: c[0 .. la+lb-1) = a * b mod p.  a, b, c may be host memory

@@ -14,13 +14,20 @@
 // polymul_batch.cu, whose builder groups products by padded size), and copies
 // of the results back.  Requests that arrive while batches run are admitted as
 // memory frees up and launched on the next idle slot, so their work overlaps
-// with the batches already on the device.  Twiddle tables for the server's
+// with the batches already on the device.  Each slot has a launcher thread
+// that builds its batch and queues the copies and kernels, so the host work of
+// several batches proceeds in parallel.  Twiddle tables for the server's
 // primes are built once and stay resident; the device job and product tables
 // of each slot are reused across batches.  Small requests' copies are one
 // copy-kernel launch per direction and batch; large ones use the copy
 // engines.
+#include <atomic>
+#include <condition_variable>
 #include <deque>
 #include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
 #include <vector>
 
 #include "batch_internal.cuh"
@@ -113,10 +120,20 @@ struct Req {
     uint32_t *da = nullptr, *db = nullptr, *dc = nullptr, *dws = nullptr;
 };
 
+// A slot's batch moves IDLE -> PENDING (requests handed to the slot's
+// launcher thread) -> LAUNCHED (copies and kernels queued on its stream, or
+// launch_rc set) -> IDLE (retired by progress once its event completes).
+enum SlotState : int { SLOT_IDLE = 0, SLOT_PENDING = 1, SLOT_LAUNCHED = 2 };
+
 struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
-    bool busy = false;
+    std::atomic<int> state{SLOT_IDLE};
+    int launch_rc = MONT_OK;
+    std::thread worker;
+    std::mutex mu;
+    std::condition_variable cv;
+    bool stop = false;
     std::vector<Req> reqs;
     Job *d_jobs = nullptr;
     Prod *d_prods = nullptr;
@@ -148,7 +165,7 @@ struct mont_server {
     uint8_t *arena_base = nullptr;
     mont::Arena arena;
     size_t max_batch_coeffs = 0;
-    std::vector<mont::Slot> slots;
+    std::vector<std::unique_ptr<mont::Slot>> slots;
     std::deque<mont::Req> queued, admitted;
     std::deque<mont_completion> completed;
     mont_server_stats stats{};
@@ -214,18 +231,22 @@ size_t request_bytes(const mont_request &r)
 // Finished batches: report completions and free their memory.
 void retire(mont_server *sv)
 {
-    for (Slot &s : sv->slots) {
-        if (!s.busy) continue;
-        const cudaError_t q = cudaEventQuery(s.done);
-        if (q == cudaErrorNotReady) continue;
-        const int status = q != cudaSuccess ? MONT_ECUDA : (*s.h_err ? MONT_ETIMEOUT : MONT_OK);
+    for (auto &sp : sv->slots) {
+        Slot &s = *sp;
+        if (s.state.load(std::memory_order_acquire) != SLOT_LAUNCHED) continue;
+        int status = s.launch_rc;
+        if (status == MONT_OK) {
+            const cudaError_t q = cudaEventQuery(s.done);
+            if (q == cudaErrorNotReady) continue;
+            status = q != cudaSuccess ? MONT_ECUDA : (*s.h_err ? MONT_ETIMEOUT : MONT_OK);
+        }
         for (const Req &r : s.reqs) {
             sv->arena.release(r.off, r.bytes);
             sv->completed.push_back(mont_completion{r.r.id, status, 0});
             sv->stats.completed++;
         }
         s.reqs.clear();
-        s.busy = false;
+        s.state.store(SLOT_IDLE, std::memory_order_release);
     }
 }
 
@@ -252,9 +273,10 @@ void admit(mont_server *sv)
     }
 }
 
-int launch_slot(mont_server *sv, Slot &s)
+// Main thread: move admitted requests (arrival order, up to the coefficient
+// cap) into an idle slot and hand them to its launcher thread.
+void take_batch(mont_server *sv, Slot &s)
 {
-    // Take admitted requests in arrival order up to the coefficient cap.
     size_t coeffs = 0;
     while (!sv->admitted.empty()) {
         const Req &q = sv->admitted.front();
@@ -264,7 +286,20 @@ int launch_slot(mont_server *sv, Slot &s)
         s.reqs.push_back(q);
         sv->admitted.pop_front();
     }
-    if (s.reqs.empty()) return MONT_OK;
+    if (s.reqs.empty()) return;
+    sv->stats.batches++;
+    sv->stats.launched += s.reqs.size();
+    {
+        std::lock_guard<std::mutex> lock(s.mu);
+        s.state.store(SLOT_PENDING, std::memory_order_release);
+    }
+    s.cv.notify_one();
+}
+
+// Launcher thread: build the batch and queue copies, kernels and the
+// completion event on the slot's stream.
+int issue_batch(mont_server *sv, Slot &s)
+{
     std::vector<polymul_desc> descs(s.reqs.size());
     for (size_t i = 0; i < s.reqs.size(); i++) {
         const Req &q = s.reqs[i];
@@ -346,23 +381,37 @@ int launch_slot(mont_server *sv, Slot &s)
     if (rc != MONT_OK) {
         cudaStreamSynchronize(s.stream);
         cudaGetLastError();
-        for (const Req &q : s.reqs) {
-            sv->arena.release(q.off, q.bytes);
-            sv->completed.push_back(mont_completion{q.r.id, rc, 0});
-            sv->stats.completed++;
-        }
-        s.reqs.clear();
-        return rc;
     }
-    s.busy = true;
-    sv->stats.batches++;
-    sv->stats.launched += s.reqs.size();
-    return MONT_OK;
+    return rc;
+}
+
+void worker_loop(mont_server *sv, Slot *s)
+{
+    cudaSetDevice(sv->device);
+    for (;;) {
+        std::unique_lock<std::mutex> lock(s->mu);
+        s->cv.wait(lock, [&] { return s->stop || s->state.load(std::memory_order_acquire) == SLOT_PENDING; });
+        if (s->stop) return;
+        lock.unlock();
+        s->launch_rc = issue_batch(sv, *s);
+        s->state.store(SLOT_LAUNCHED, std::memory_order_release);
+    }
 }
 
 void destroy_server(mont_server *sv)
 {
-    for (Slot &s : sv->slots) {
+    for (auto &sp : sv->slots) {
+        if (!sp || !sp->worker.joinable()) continue;
+        {
+            std::lock_guard<std::mutex> lock(sp->mu);
+            sp->stop = true;
+        }
+        sp->cv.notify_one();
+        sp->worker.join();
+    }
+    for (auto &sp : sv->slots) {
+        if (!sp) continue;
+        Slot &s = *sp;
         if (s.stream) cudaStreamSynchronize(s.stream);
         cudaFree(s.d_jobs);
         cudaFree(s.d_prods);
@@ -406,9 +455,9 @@ extern "C" int mont_server_create(const uint32_t *primes, int nprimes, uint32_t 
     sv->sms = device_sm_count();
     if (rc == MONT_OK && sv->sms <= 0) rc = MONT_ECUDA;
     if (rc == MONT_OK && cudaMalloc(&sv->arena_base, budget_bytes) != cudaSuccess) rc = MONT_ENOMEM;
-    sv->slots.resize(slots);
+    for (int i = 0; i < slots; i++) sv->slots.push_back(std::make_unique<Slot>());
     for (int i = 0; i < slots && rc == MONT_OK; i++) {
-        Slot &s = sv->slots[i];
+        Slot &s = *sv->slots[i];
         if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess ||
             cudaMallocHost(&s.h_err, sizeof(uint32_t)) != cudaSuccess)
@@ -427,6 +476,7 @@ extern "C" int mont_server_create(const uint32_t *primes, int nprimes, uint32_t 
     sv->args.wait_iters = 1u << 22;
     sv->args.wait_ns = 2000000000ull;
     sv->stats.budget_bytes = budget_bytes;
+    for (auto &sp : sv->slots) sp->worker = std::thread(worker_loop, sv, sp.get());
     *out = sv;
     return MONT_OK;
 }
@@ -472,10 +522,9 @@ extern "C" int mont_server_progress(mont_server *sv, mont_completion *done, size
     retire(sv);
     admit(sv);
     int rc = MONT_OK;
-    for (Slot &s : sv->slots) {
-        if (s.busy || sv->admitted.empty()) continue;
-        const int r = launch_slot(sv, s);
-        if (r != MONT_OK) rc = r;
+    for (auto &sp : sv->slots) {
+        if (sv->admitted.empty()) break;
+        if (sp->state.load(std::memory_order_acquire) == SLOT_IDLE) take_batch(sv, *sp);
     }
     sv->stats.bytes_in_use = sv->arena.used();
     size_t k = 0;
@@ -494,7 +543,7 @@ extern "C" int mont_server_get_stats(const mont_server *sv, mont_server_stats *o
     out->queued = sv->queued.size();
     out->admitted_waiting = sv->admitted.size();
     size_t inflight = 0;
-    for (const mont::Slot &s : sv->slots) inflight += s.reqs.size();
+    for (const auto &sp : sv->slots) inflight += sp->reqs.size();
     out->in_flight = inflight;
     return MONT_OK;
 }
