@@ -79,7 +79,7 @@ k_ntt_fwd(NttArgs A)
     __syncthreads();
     fwd_passes<LOGN, NT, 1, true, 0, NP - 1>(lay, tid, A.tw, 0, 0, Mod{A.p, A.pp});
     if (valid)
-        for (int k = tid; k < N; k += NT) g[k] = lay[0][A.bitrev ? k : brev<LOGN>(k)];
+        for (int k = tid; k < N; k += NT) g[k] = csub(lay[0][A.bitrev ? k : brev<LOGN>(k)], A.p);
 }
 
 // In-place inverse NTT (with the factor N^-1) of [batch][N]; natural (or,

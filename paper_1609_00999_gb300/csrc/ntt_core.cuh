@@ -35,18 +35,44 @@ struct Mod {
     uint32_t pp;   // P' = -P^-1 mod 2^32
 };
 
-// CT butterfly, all values in [0, P).
+// Forward values are kept lazily in [0, 2P): with P < 2^31, 2P < R, so the
+// sum of two reduced values fits 32 bits, and REDC of a lazy value by a
+// reduced twiddle (T < 2P^2 < RP) is below 2P.  Each CT butterfly therefore
+// reduces its inputs rather than its outputs (one conditional subtract fewer),
+// and level 0, whose inputs are the transform's reduced input, reduces
+// nothing.  Whoever consumes a forward result reduces it: the pointwise
+// product reduces one factor (REDC of [0, P) x [0, 2P) is below 2P), the
+// stand-alone forward transform reduces on store.  Inverse (GS) values stay
+// in [0, P).
+
+// CT butterfly: x, y in [0, 2P) -> x + r y, x - r y in [0, 2P).
 __device__ __forceinline__ void bfly_ct(uint32_t &x, uint32_t &y, uint32_t w, Mod m)
 {
     const uint32_t t = csub(redc_lazy(y, w, m.p, m.pp), m.p);
-    const uint32_t s = x + t;
-    const uint32_t d = x - t + m.p;
-    x = csub(s, m.p);
-    y = csub(d, m.p);
+    const uint32_t u = csub(x, m.p);
+    x = u + t;
+    y = u - t + m.p;
 }
 
-// Butterfly with twiddle 1 (same for CT and GS).
-__device__ __forceinline__ void bfly_one(uint32_t &x, uint32_t &y, Mod m)
+// CT butterfly with twiddle 1, [0, 2P) in and out.
+__device__ __forceinline__ void bfly_ct_one(uint32_t &x, uint32_t &y, Mod m)
+{
+    const uint32_t u = csub(x, m.p);
+    const uint32_t v = csub(y, m.p);
+    x = u + v;
+    y = u - v + m.p;
+}
+
+// CT butterfly with twiddle 1 on reduced inputs (level 0): out in [0, 2P).
+__device__ __forceinline__ void bfly_ct_first(uint32_t &x, uint32_t &y, Mod m)
+{
+    const uint32_t s = x + y;
+    y = x - y + m.p;
+    x = s;
+}
+
+// GS butterfly with twiddle 1, all values in [0, P).
+__device__ __forceinline__ void bfly_gs_one(uint32_t &x, uint32_t &y, Mod m)
 {
     const uint32_t s = x + y;
     const uint32_t d = x - y + m.p;
@@ -95,7 +121,8 @@ __device__ __forceinline__ void load_tw(uint32_t (&w)[CNT], const uint32_t *__re
 // One forward level (local level L of a group of 2^E elements): 2^L local
 // blocks, block lb uses twiddle index 2^(s_abs+L) + (blk << L) + lb.
 // FIRST_BLOCK: the group lies in block 0 of the transform at every level
-// (blk == 0 and s_abs == 0), so local block 0 has twiddle 1.
+// (blk == 0 and s_abs == 0), so local block 0 has twiddle 1, and local
+// level 0 is level 0 of the transform (reduced inputs).
 template <int E, int L, int NARR, bool FIRST_BLOCK>
 __device__ __forceinline__ void ct_level(uint32_t (&x)[NARR][1 << E], const uint32_t *__restrict__ tw, int s_abs,
                                          int blk, Mod m)
@@ -111,8 +138,12 @@ __device__ __forceinline__ void ct_level(uint32_t (&x)[NARR][1 << E], const uint
             for (int a = 0; a < NARR; a++) {
                 uint32_t &x0 = x[a][lb * 2 * HALF + u];
                 uint32_t &x1 = x[a][lb * 2 * HALF + u + HALF];
-                if (FIRST_BLOCK && lb == 0) bfly_one(x0, x1, m);
-                else bfly_ct(x0, x1, w[lb], m);
+                if (FIRST_BLOCK && lb == 0) {
+                    if constexpr (L == 0) bfly_ct_first(x0, x1, m);
+                    else bfly_ct_one(x0, x1, m);
+                } else {
+                    bfly_ct(x0, x1, w[lb], m);
+                }
             }
 }
 
@@ -131,7 +162,7 @@ __device__ __forceinline__ void gs_level(uint32_t (&x)[NARR][1 << E], const uint
             for (int a = 0; a < NARR; a++) {
                 uint32_t &x0 = x[a][lb * 2 * HALF + u];
                 uint32_t &x1 = x[a][lb * 2 * HALF + u + HALF];
-                if (FIRST_BLOCK && lb == 0) bfly_one(x0, x1, m);
+                if (FIRST_BLOCK && lb == 0) bfly_gs_one(x0, x1, m);
                 else bfly_gs(x0, x1, w[lb], m);
             }
 }
@@ -305,7 +336,8 @@ __device__ __forceinline__ void inv_passes(const L &lay, int tid, const uint32_t
     }
 }
 
-// Last forward pass of both operands, pointwise REDC product (A B~ R^-1),
+// Last forward pass of both operands, pointwise REDC product (A B~ R^-1, one
+// lazy factor reduced first),
 // then the same levels of the inverse in reverse, result into lay[0].
 template <int LOGN, int NT, bool BASE0, class L>
 __device__ __forceinline__ void fused_middle_pass(const L (&lay)[2], int tid, const uint32_t *__restrict__ tw,
@@ -324,7 +356,7 @@ __device__ __forceinline__ void fused_middle_pass(const L (&lay)[2], int tid, co
         ct_group<PL::E, 2, BASE0 && PL::S0 == 0>(x, tw, s_base + PL::S0, blk, m);
         uint32_t y[1][PL::G];
 #pragma unroll
-        for (int t = 0; t < PL::G; t++) y[0][t] = mont_mul(x[0][t], x[1][t], m.p, m.pp);
+        for (int t = 0; t < PL::G; t++) y[0][t] = mont_mul(csub(x[0][t], m.p), x[1][t], m.p, m.pp);
         gs_group<PL::E, 1, BASE0 && PL::S0 == 0>(y, itw, s_base + PL::S0, blk, m);
 #pragma unroll
         for (int t = 0; t < PL::G; t++) elem(lay[0], base, t * PL::HMIN) = y[0][t];

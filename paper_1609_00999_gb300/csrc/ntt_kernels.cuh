@@ -23,13 +23,13 @@ constexpr int teams_of()
     return nt_of<LOGN>() >= 256 ? 1 : 256 / nt_of<LOGN>();
 }
 
-// CTAs per SM the register budget is sized for: three 256-thread CTAs
-// (at most 85 registers per thread) for the fused products up to 2^12;
+// CTAs per SM the register budget is sized for: four 256-thread CTAs
+// (64 registers per thread, no spills) for the fused products up to 2^12;
 // one CTA for the 512- and 1024-thread transforms.
 template <int LOGN>
 constexpr int min_ctas_of()
 {
-    return teams_of<LOGN>() * nt_of<LOGN>() <= 256 ? 3 : 1;
+    return teams_of<LOGN>() * nt_of<LOGN>() <= 256 ? 4 : 1;
 }
 
 // Shared-memory words one team needs for a product of 2^LOGN (both operands,
@@ -99,7 +99,7 @@ __device__ __forceinline__ void polymul_team(uint32_t *sm, int tid, const uint32
                 ct_group<P0::E, 2, BASE0>(x, tw, s_base, b_idx, md);
                 uint32_t y[1][P0::G];
 #pragma unroll
-                for (int t = 0; t < P0::G; t++) y[0][t] = mont_mul(x[0][t], x[1][t], p, pp);
+                for (int t = 0; t < P0::G; t++) y[0][t] = mont_mul(csub(x[0][t], p), x[1][t], p, pp);
                 gs_group<P0::E, 1, BASE0>(y, itw, s_base, b_idx, md);
 #pragma unroll
                 for (int t = 0; t < P0::G; t++) {

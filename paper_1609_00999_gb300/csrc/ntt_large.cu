@@ -11,7 +11,9 @@
 // Column kernel: a CTA loads a tile of C consecutive columns with coalesced
 // row segments, runs the column levels per column (one team of threads per
 // column), and writes the tile back.  Row kernel: one CTA per row, the same
-// register passes as the single-CTA kernels.
+// register passes as the single-CTA kernels.  Forward values between the
+// column and row kernels are lazy ([0, 2P), as inside the passes); the row
+// kernels take them as such and reduce what they finally store.
 #include <algorithm>
 
 #include "ntt_kernels.cuh"
@@ -134,7 +136,7 @@ k_row_ntt(RowNttArgs A, size_t prod0)
     __syncthreads();
     if constexpr (!INVERSE) fwd_passes<K2, NT, 1, false, 0, NP - 1>(lay, threadIdx.x, A.tw, A.k1, r, Mod{A.p, A.pp});
     else inv_passes<K2, NT, false, NP - 1, 0>(lay[0], threadIdx.x, A.tw, A.k1, r, Mod{A.p, A.pp});
-    for (int k = threadIdx.x; k < N2; k += NT) g[k] = lay[0][k];
+    for (int k = threadIdx.x; k < N2; k += NT) g[k] = INVERSE ? lay[0][k] : csub(lay[0][k], A.p);
 }
 
 // In-place bit-reversal permutation of each row of 2^log2n elements.

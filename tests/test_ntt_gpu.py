@@ -109,6 +109,24 @@ def test_polymul_adversarial_values(m):
             assert np.array_equal(got, oracle.polymul_schoolbook(p, a, b))
 
 
+@pytest.mark.parametrize("logn", [1, 2, 5, 11, 12, 14])
+def test_ntt_extreme_inputs(m, logn):
+    """Inputs at the top of the residue range: the forward passes keep values
+    in [0, 2P), so P - 1 everywhere (and alternating with 0) drives the
+    intermediate sums closest to 2^32 for the largest prime."""
+    n = 1 << logn
+    for p in synth.PRIMES:
+        x = np.stack([np.full(n, p - 1, dtype=np.uint32),
+                      np.where(np.arange(n) % 2 == 0, p - 1, 0).astype(np.uint32),
+                      np.where(np.arange(n) < n // 2, p - 1, p - 2).astype(np.uint32)])
+        plan = m.ntt_plan_create(p, logn)
+        d = to_dev(x)
+        m.ntt_fwd(plan, d)
+        assert np.array_equal(to_host(d).reshape(3, n), oracle_rows(p, x))
+        m.ntt_inv(plan, d)
+        assert np.array_equal(to_host(d).reshape(3, n), x)
+
+
 def test_polymul_errors(m):
     import torch
     d = to_dev(np.zeros(8, dtype=np.uint32))

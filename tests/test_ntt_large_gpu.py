@@ -68,6 +68,23 @@ def test_large_polymul(m, p, la, lb):
         assert np.array_equal(got[idx], sb[idx])
 
 
+@pytest.mark.parametrize("p", synth.PRIMES)
+def test_large_extreme_inputs(m, p):
+    """P - 1 everywhere through the column / row kernels (forward values are
+    lazy between them)."""
+    la, lb = 20000, 13000
+    a = np.full(la, p - 1, dtype=np.uint32)
+    b = np.full(lb, p - 1, dtype=np.uint32)
+    got = to_host(m.polymul(p, to_dev(a), to_dev(b)))
+    assert np.array_equal(got, oracle.polymul_ntt(p, a, b))
+    logn = 16
+    x = np.full((1, 1 << logn), p - 1, dtype=np.uint32)
+    plan = m.ntt_plan_create(p, logn)
+    d = to_dev(x)
+    m.ntt_fwd(plan, d)
+    assert np.array_equal(to_host(d).reshape(1, -1), np.stack([oracle.ntt(p, x[0])]))
+
+
 def test_large_polymul_many_and_chunked_workspace(m):
     import torch
     p, count, la, lb = synth.P2, 5, 20000, 12001
