@@ -167,9 +167,9 @@ __device__ __forceinline__ void small_dispatch(uint32_t *smem, const BatchArgs &
     }
 }
 
-// MINB: CTAs per SM the registers are budgeted for (2: 128 registers, no
-// spills; 3: 80 registers with a few spills, more warps to hide memory
-// latency).  The autotuner picks one.
+// MINB: CTAs per SM the registers are budgeted for (2: up to 128 registers;
+// 3: up to 85, more warps to hide memory latency; neither spills).  The
+// autotuner picks one.
 template <int MINB>
 __global__ void __launch_bounds__(kThreads, MINB) k_polymul_batch(BatchArgs A)
 {
