@@ -184,7 +184,7 @@ def uneven_batch(m, torch, peaks, steps=10, warmup=3, cpu=True, per_product=True
     return res
 
 
-def serve_stream(m, torch, n=50000, budget=16 << 30, slots=4, batch_coeffs=1 << 27, load=0.8, pool_log2=24,
+def serve_stream(m, torch, n=50000, budget=16 << 30, slots=4, batch_coeffs=1 << 24, load=0.8, pool_log2=24,
                  ring_words=1 << 30):
     lens = synth.loguniform_lengths(n, 1 << 8, 1 << 20, synth.SEED_SERVE, 0)
     primes = synth.choose_primes(n, synth.SEED_SERVE, 1)

@@ -225,7 +225,7 @@ typedef struct polymul_batch_config {
 } polymul_batch_config;
 
 /* Library-owned plan: device copies of the job list and the product table,
- * synchronisation counters, scratch (2N words per product with N > 2^12),
+ * synchronisation counters, scratch (2N words per product with N > 2^13),
  * resident twiddle tables and, once used, a CUDA graph.  Creation allocates
  * and copies synchronously (not during stream capture).  Up to 8 distinct
  * primes per batch (else MONT_EUNSUPPORTED). */
@@ -262,7 +262,7 @@ int polymul_batch_plan_set_wait_limit(polymul_batch_plan *plan, uint32_t iterati
 /* Failure-detection test hook: makes the first split product wait for a
  * column tile that does not exist, so its bounded waits expire and
  * polymul_batch_status reports MONT_ETIMEOUT.  MONT_EINVAL if the batch has
- * no product with N > 2^12. */
+ * no product with N > 2^13. */
 int polymul_batch_plan_inject_stall(polymul_batch_plan *plan);
 
 /* ------------------------------------------------------------------------

@@ -9,7 +9,8 @@
 namespace mont {
 
 constexpr int kThreads = 256;         // threads per CTA of the persistent kernel
-constexpr int kRowLog = 12;        // row size 2^12 for split products
+constexpr int kSmallLog = 13;      // N <= 2^13: whole product in one CTA
+constexpr int kRowLog = 12;        // row size 2^12 for split products (N > 2^13)
 constexpr int kMaxColLog = 9;      // K1 <= 9: N <= 2^21 in a batch
 constexpr int kMaxPrimes = 8;
 
@@ -61,7 +62,7 @@ struct BatchHost {
 };
 
 // Validates the descriptors and builds the batch.  Products are stored small
-// (N <= 2^12, sorted by size) first, then split ones.  Primes are looked up
+// (N <= 2^13, sorted by size) first, then split ones.  Primes are looked up
 // in prime_list (extended, and prime_log2 raised, unless fixed_primes).
 int batch_build(const polymul_desc *descs, size_t count, BatchHost &out, std::vector<uint32_t> &prime_list,
                 std::vector<int> &prime_log2, bool fixed_primes);
@@ -73,7 +74,7 @@ int batch_occupancy(int variant, int *per_sm);
 // Resets the counters (sync_words words) and launches `grid` CTAs on jobs.
 int batch_launch(BatchArgs A, const Job *jobs, uint32_t njobs, size_t sync_words, int grid, int variant,
                  cudaStream_t s);
-// Scratch words for one product of this output length (0 when N <= 2^12).
+// Scratch words for one product of this output length (0 when N <= 2^13).
 size_t batch_ws_words(size_t lc);
 
 }  // namespace mont

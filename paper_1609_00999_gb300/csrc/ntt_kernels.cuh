@@ -59,21 +59,22 @@ int ensure_smem(K kernel, size_t bytes)
                : MONT_ECUDA;
 }
 
-// One product (or one row block of a product) by one team of nt_of<LOGN>()
-// threads with team_smem_words<LOGN>() words of shared memory at sm:
+// One product (or one row block of a product) by one team of NT threads
+// (nt_of<LOGN>() by default, fewer when each thread takes several groups per
+// pass) with team_smem_words<LOGN>() words of shared memory at sm:
 // c[0 .. lc) = inverse( forward(a) * forward(b * scale) ), where the
 // sub-transform is block b_idx of the levels s_base .. s_base + LOGN - 1 of
 // the whole transform (s_base = 0, b_idx = 0 for a complete product).
 // Reads of a and b (lengths la, lb, zero beyond) all happen before the first
 // barrier, so gc may alias ga (in-place row passes).  Every thread of the CTA
 // must call it (it contains __syncthreads).  la, lb, lc <= 2^LOGN.
-template <int LOGN, bool BASE0, bool SCALE_B>
+template <int LOGN, bool BASE0, bool SCALE_B, int NT = nt_of<LOGN>()>
 __device__ __forceinline__ void polymul_team(uint32_t *sm, int tid, const uint32_t *ga, size_t la,
                                              const uint32_t *gb, size_t lb, uint32_t *gc, size_t lc,
                                              const uint32_t *__restrict__ tw, const uint32_t *__restrict__ itw, int s_base,
                                              int b_idx, uint32_t p, uint32_t pp, uint32_t k_scale)
 {
-    constexpr int N = 1 << LOGN, NT = nt_of<LOGN>(), NP = Sched<LOGN>::kPasses;
+    constexpr int N = 1 << LOGN, NP = Sched<LOGN>::kPasses;
     const Mod md{p, pp};
     if constexpr (LOGN == 0) {
         if (lc > 0) {

@@ -1,14 +1,15 @@
 // polymul_batch.cu -- many products of uneven sizes and mixed primes in ONE
 // persistent kernel launch (optionally replayed as a CUDA graph).
 //
-// The host turns the batch into a job list.  A product with N <= 2^12 is
+// The host turns the batch into a job list.  A product with N <= 2^13 is
 // computed whole by one team of threads (SMALL job; a job covers as many
-// products of one size as fit in a 256-thread CTA).  A product with
-// N = 2^K > 2^12 is split as in ntt_large.cu (K1 = K - 12 column levels,
-// rows of 2^12): COLF jobs run the forward column levels of both operands on
-// one column tile, ROW jobs run one row (forward row levels, pointwise
-// product, inverse row levels), COLI jobs run the inverse column levels of
-// one tile and write c.  Scratch: 2N words per large product.
+// products of one size as fit in a 256-thread CTA; 2^12 and 2^13 take the
+// whole CTA).  A product with N = 2^K > 2^13 is split as in ntt_large.cu
+// (K1 = K - 12 column levels, rows of 2^12): COLF jobs run the forward
+// column levels of both operands on one column tile, ROW jobs run one row
+// (forward row levels, pointwise product, inverse row levels), COLI jobs run
+// the inverse column levels of one tile and write c.  Scratch: 2N words per
+// large product.
 //
 // CTAs of the persistent grid claim jobs in list order with one atomic
 // counter.  A ROW job waits until every COLF tile of its product has
@@ -28,22 +29,43 @@
 namespace mont {
 namespace {
 
-// Column tile geometry for a 256-thread CTA: C columns of N1 = 2^K1, NT1
-// threads per column; layouts chosen (as in ntt_large.cu) for conflict-free
-// tile loads and nearly conflict-free pass accesses.
-template <int K1>
-struct Col256 {
-    static constexpr int N1 = 1 << K1;
-    static constexpr int NT1 = N1 <= 16 ? 1 : N1 / 16;
-    static constexpr int C = kThreads / NT1;
-    static constexpr int PAD = K1 <= 4 ? 1 : 0;
-    static constexpr int MUL = K1 <= 4 ? 0 : ((K1 == 5 || K1 == 8) ? 17 : 9);
-    static constexpr bool SW = K1 >= 8;
-    static constexpr int STRIDE = N1 + PAD;
-    static constexpr int WORDS = C * STRIDE;
-};
+// Shared memory per CTA: one 2^13 product (both operands, padded layout).
+constexpr int kSmemWords = team_smem_words<kSmallLog>();
 
-constexpr int kSmemWords = 2 * 4352 > team_smem_words<kRowLog>() ? 2 * 4352 : team_smem_words<kRowLog>();
+// Column tile geometry for a 256-thread CTA: columns of N1 = 2^K1 at stride
+// N1 + PAD, NT1 threads per column, C0 = 256 / NT1 columns per round and C
+// columns per tile, so each thread runs ROUNDS = C / C0 columns one after
+// the other.  Layouts as in ntt_large.cu: column c XORs its low five bits
+// with (c * MUL) & 31, which makes the tile loads conflict-free and the pass
+// accesses nearly so.  Where that pattern repeats every C0 columns (every
+// round then sees the same banks), C is the most columns (a power of two, at
+// most a row) whose two operands fit kSmemWords; otherwise C = C0.
+constexpr int col_nt1(int k1) { return k1 <= 4 ? 1 : (1 << k1) / 16; }
+constexpr int col_mul(int k1) { return k1 <= 4 ? 0 : ((k1 == 5 || k1 == 8) ? 17 : 9); }
+constexpr int col_stride(int k1) { return (1 << k1) + (k1 <= 4 ? 1 : 0); }
+constexpr int col_tile_cols(int k1)
+{
+    const int c0 = kThreads / col_nt1(k1);
+    if ((c0 * col_mul(k1)) % 32 != 0) return c0;
+    int c = 1 << kRowLog;
+    while (c > c0 && 2 * c * col_stride(k1) > kSmemWords) c >>= 1;
+    return c;
+}
+
+template <int K1>
+struct ColTile {
+    static constexpr int N1 = 1 << K1;
+    static constexpr int NT1 = col_nt1(K1);
+    static constexpr int C0 = kThreads / NT1;
+    static constexpr int C = col_tile_cols(K1);
+    static constexpr int ROUNDS = C / C0;
+    static constexpr int MUL = col_mul(K1);
+    static constexpr bool SW = K1 >= 8;
+    static constexpr int STRIDE = col_stride(K1);
+    static constexpr int WORDS = C * STRIDE;
+    static_assert(ROUNDS >= 1 && C % C0 == 0 && (ROUNDS == 1 || (C0 * MUL) % 32 == 0), "column tile geometry");
+    static_assert(2 * WORDS <= kSmemWords, "column tile does not fit");
+};
 
 __device__ __forceinline__ unsigned long long globaltimer()
 {
@@ -76,7 +98,7 @@ __device__ bool bounded_wait(const uint32_t *ctr, uint32_t target, const BatchAr
 template <int K1, bool INV>
 __device__ __forceinline__ void col_tile(uint32_t *smem, const Prod &P, const PrimeInfo &pr, uint32_t tile)
 {
-    using CF = Col256<K1>;
+    using CF = ColTile<K1>;
     constexpr int NP = Sched<K1>::kPasses;
     constexpr int NARR = INV ? 1 : 2;
     const size_t n = size_t{1} << P.k;
@@ -98,12 +120,16 @@ __device__ __forceinline__ void col_tile(uint32_t *smem, const Prod &P, const Pr
         }
     }
     __syncthreads();
-    const int c = threadIdx.x / CF::NT1, tid = threadIdx.x % CF::NT1;
-    if constexpr (!INV) {
-        const ColLayout<CF::SW> lay[2] = {col(0, c), col(1, c)};
-        fwd_passes<K1, CF::NT1, 2, true, 0, NP - 1>(lay, tid, pr.tw, 0, 0, md);
-    } else {
-        inv_passes<K1, CF::NT1, true, NP - 1, 0>(col(0, c), tid, pr.itw, 0, 0, md);
+    const int tid = threadIdx.x % CF::NT1;
+#pragma unroll 1
+    for (int r = 0; r < CF::ROUNDS; r++) {
+        const int c = threadIdx.x / CF::NT1 + r * CF::C0;
+        if constexpr (!INV) {
+            const ColLayout<CF::SW> lay[2] = {col(0, c), col(1, c)};
+            fwd_passes<K1, CF::NT1, 2, true, 0, NP - 1>(lay, tid, pr.tw, 0, 0, md);
+        } else {
+            inv_passes<K1, CF::NT1, true, NP - 1, 0>(col(0, c), tid, pr.itw, 0, 0, md);
+        }
     }
 #pragma unroll
     for (int a = 0; a < NARR; a++) {
@@ -121,7 +147,6 @@ template <bool INV>
 __device__ __forceinline__ void col_job(uint32_t *smem, const Prod &P, const PrimeInfo &pr, uint32_t tile)
 {
     switch (P.k - kRowLog) {
-    case 1: col_tile<1, INV>(smem, P, pr, tile); break;
     case 2: col_tile<2, INV>(smem, P, pr, tile); break;
     case 3: col_tile<3, INV>(smem, P, pr, tile); break;
     case 4: col_tile<4, INV>(smem, P, pr, tile); break;
@@ -137,13 +162,13 @@ __device__ __forceinline__ void col_job(uint32_t *smem, const Prod &P, const Pri
 template <int K>
 __device__ __forceinline__ void small_job(uint32_t *smem, const BatchArgs &A, const Job &J)
 {
-    constexpr int NT = nt_of<K>(), T = kThreads / NT, N = 1 << K;
+    constexpr int NT = nt_of<K>() < kThreads ? nt_of<K>() : kThreads, T = kThreads / NT;
     const int team = threadIdx.x / NT, tid = threadIdx.x - team * NT;
     const bool valid = static_cast<uint32_t>(team) < J.idx;
     const Prod &P = A.prods[J.prod + (valid ? team : 0)];
     const PrimeInfo &pr = A.primes[P.prime];
     static_assert(T * team_smem_words<K>() <= kSmemWords, "small job does not fit");
-    polymul_team<K, true, true>(smem + team * team_smem_words<K>(), tid, P.a, valid ? P.la : 0, P.b, valid ? P.lb : 0, P.c,
+    polymul_team<K, true, true, NT>(smem + team * team_smem_words<K>(), tid, P.a, valid ? P.la : 0, P.b, valid ? P.lb : 0, P.c,
                                 valid ? P.lc : 0, pr.tw, pr.itw, 0, 0, pr.p, pr.pp, P.k_scale);
 }
 
@@ -163,12 +188,13 @@ __device__ __forceinline__ void small_dispatch(uint32_t *smem, const BatchArgs &
     case 10: small_job<10>(smem, A, J); break;
     case 11: small_job<11>(smem, A, J); break;
     case 12: small_job<12>(smem, A, J); break;
+    case 13: small_job<13>(smem, A, J); break;
     default: break;
     }
 }
 
 // MINB: CTAs per SM the registers are budgeted for (2: up to 128 registers;
-// 3: up to 85, more warps to hide memory latency; neither spills).  The
+// 3: up to 85, a few spills, more warps to hide memory latency).  The
 // autotuner picks one.
 template <int MINB>
 __global__ void __launch_bounds__(kThreads, MINB) k_polymul_batch(BatchArgs A)
@@ -225,15 +251,13 @@ __global__ void __launch_bounds__(kThreads, MINB) k_polymul_batch(BatchArgs A)
 
 int col_tiles(int k1)
 {
-    const int nt1 = k1 <= 4 ? 1 : (1 << k1) / 16;
-    const int c = kThreads / nt1;
-    return (1 << kRowLog) / c;
+    return (1 << kRowLog) / col_tile_cols(k1);
 }
 
 int teams_for(int k)
 {
     const int nt = k <= 4 ? 1 : (1 << (k - 4));
-    return kThreads / nt;
+    return nt >= kThreads ? 1 : kThreads / nt;
 }
 
 }  // namespace
@@ -241,7 +265,7 @@ int teams_for(int k)
 size_t batch_ws_words(size_t lc)
 {
     const int k = ceil_log2(lc);
-    return k > kRowLog ? (size_t{2} << k) : 0;
+    return k > kSmallLog ? (size_t{2} << k) : 0;
 }
 
 int batch_build(const polymul_desc *descs, size_t count, BatchHost &out, std::vector<uint32_t> &prime_list,
@@ -288,7 +312,7 @@ int batch_build(const polymul_desc *descs, size_t count, BatchHost &out, std::ve
         const uint32_t n_mod = static_cast<uint32_t>((uint64_t{1} << k) % d.p);
         P.k_scale = host_to_mont(host_to_mont(host_powmod(n_mod, d.p - 2, d.p), d.p), d.p);   // N^-1 R^2
         P.ntiles = P.nrows = 0;
-        if (k > kRowLog) {
+        if (k > kSmallLog) {
             P.ntiles = static_cast<uint32_t>(col_tiles(k - kRowLog));
             P.nrows = 1u << (k - kRowLog);
             P.ws = reinterpret_cast<uint32_t *>(out.ws_words);   // word offset until rebased
@@ -359,7 +383,7 @@ int batch_build(const polymul_desc *descs, size_t count, BatchHost &out, std::ve
 void batch_rebase(BatchHost &b, uint32_t *ws)
 {
     for (Prod &P : b.prods)
-        if (P.k > static_cast<uint32_t>(kRowLog)) P.ws = ws + reinterpret_cast<size_t>(P.ws);
+        if (P.k > static_cast<uint32_t>(kSmallLog)) P.ws = ws + reinterpret_cast<size_t>(P.ws);
 }
 
 int batch_occupancy(int variant, int *per_sm)
@@ -654,7 +678,7 @@ extern "C" int polymul_batch_plan_inject_stall(polymul_batch_plan *plan)
     if (!plan) return MONT_EINVAL;
     for (size_t i = 0; i < plan->host.prods.size(); i++) {
         mont::Prod &P = plan->host.prods[i];
-        if (P.k <= static_cast<uint32_t>(mont::kRowLog)) continue;
+        if (P.k <= static_cast<uint32_t>(mont::kSmallLog)) continue;
         P.ntiles += 1;
         if (cudaMemcpy(plan->d_prods + i, &P, sizeof(mont::Prod), cudaMemcpyHostToDevice) != cudaSuccess)
             return MONT_ECUDA;

@@ -311,7 +311,7 @@ int issue_batch(mont_server *sv, Slot &s)
         std::map<const uint32_t *, uint32_t *> ws_of;
         for (const Req &q : s.reqs) ws_of[q.dc] = q.dws;
         for (Prod &P : s.host.prods)
-            if (P.k > static_cast<uint32_t>(kRowLog)) P.ws = ws_of[P.c];
+            if (P.k > static_cast<uint32_t>(kSmallLog)) P.ws = ws_of[P.c];
         rc = grow_slot(s, s.host.jobs[kServeOrder].size(), s.host.prods.size());
     }
     // Small requests' copies as descriptor lists for the copy kernel: operands

@@ -71,9 +71,9 @@ def test_server_rejects_bad_requests(m):
     import torch
     d = to_dev(np.ones(1 << 12, dtype=np.uint32))
     out = torch.zeros(1 << 13, dtype=torch.int32, device="cuda")
-    server = m.MontServer([synth.P1], 14, 1 << 16, slots=1)
+    server = m.MontServer([synth.P1], 14, 1 << 15, slots=1)
     big = serve.make_requests([synth.P1], [4096], [4096], [d.data_ptr()], [d.data_ptr()], [out.data_ptr()])
-    with pytest.raises(m.MontError) as e:           # needs more than the whole 64 KiB budget
+    with pytest.raises(m.MontError) as e:           # needs 64 KiB, more than the whole 32 KiB budget
         server.submit(big)
     assert e.value.code == m.MONT_ERANGE
     other = serve.make_requests([synth.P2], [8], [8], [d.data_ptr()], [d.data_ptr()], [out.data_ptr()])
