@@ -10,8 +10,9 @@ namespace mont {
 
 constexpr int kThreads = 256;         // threads per CTA of the persistent kernel
 constexpr int kSmallLog = 13;      // N <= 2^13: whole product in one CTA
-constexpr int kRowLog = 12;        // row size 2^12 for split products (N > 2^13)
-constexpr int kMaxColLog = 9;      // K1 <= 9: N <= 2^21 in a batch
+constexpr int kRowLog = 13;        // row size 2^13 for split products (N > 2^13)
+constexpr int kMaxColLog = 8;      // K1 <= 8: N <= 2^21 in a batch
+constexpr int kMaxRegColLog = 4;   // K1 <= 4: column levels in registers
 constexpr int kMaxPrimes = 8;
 
 enum : uint32_t { JOB_SMALL = 0, JOB_COLF = 1, JOB_ROW = 2, JOB_COLI = 3 };

@@ -40,6 +40,21 @@ constexpr int team_smem_words()
     return 2 * PadLayout::words(1 << LOGN);
 }
 
+// 4-byte asynchronous copy global -> shared (cp.async, no register
+// staging): a thread can have all of its tile's loads in flight at once.
+// src_bytes = 0 writes zero and reads nothing (src must still be a valid
+// address).  Completion: cp_async_wait_all, then a barrier for other threads.
+__device__ __forceinline__ void cp_async4(uint32_t *dst_smem, const uint32_t *src, uint32_t src_bytes)
+{
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst_smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 struct PolyArgs {
     const uint32_t *a, *b;
     uint32_t *c;

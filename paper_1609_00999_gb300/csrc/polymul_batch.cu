@@ -5,14 +5,16 @@
 // computed whole by one team of threads (SMALL job; a job covers as many
 // products of one size as fit in a 256-thread CTA; 2^12 and 2^13 take the
 // whole CTA).  A product with N = 2^K > 2^13 is split as in ntt_large.cu
-// (K1 = K - 12 column levels, rows of 2^12): COLF jobs run the forward
-// column levels of both operands on one column tile, ROW jobs run one row
+// (K1 = K - 13 column levels, rows of 2^13): COLF jobs run the forward
+// column levels of both operands on a block of columns, ROW jobs run one row
 // (forward row levels, pointwise product, inverse row levels), COLI jobs run
-// the inverse column levels of one tile and write c.  Scratch: 2N words per
-// large product.
+// the inverse column levels of a block of columns and write c.  Columns of
+// up to 2^4 elements are transformed in registers straight from and to
+// global memory; longer ones go through shared-memory tiles.  Scratch: 2N
+// words per large product.
 //
 // CTAs of the persistent grid claim jobs in list order with one atomic
-// counter.  A ROW job waits until every COLF tile of its product has
+// counter (each CTA one job ahead of the one it runs).  A ROW job waits until every COLF tile of its product has
 // finished, a COLI job until every ROW of its product has; both waits only
 // depend on jobs earlier in the list, which were claimed by running CTAs,
 // so the grid always makes progress.  Each wait is bounded (iterations and
@@ -95,29 +97,79 @@ __device__ bool bounded_wait(const uint32_t *ctr, uint32_t target, const BatchAr
     }
 }
 
+// A thread's share of a C x N1 column tile: PER elements, u = 0 .. PER-1, at
+// column c0 + dc(u) and row t0 + dt(u), in the order of a CTA-wide sweep of
+// the tile in row-major order (consecutive threads on consecutive columns,
+// so global accesses are coalesced).  dc(u) is a multiple of 256 columns,
+// under which the XOR pattern of ColLayout repeats, so a thread's XOR value
+// is fixed; element u then sits at a compile-time offset from the thread's
+// first element, in global memory as in shared memory.
+template <class CF>
+struct TileShare {
+    static constexpr bool WIDE = CF::C >= kThreads;
+    static constexpr int PER = CF::C * CF::N1 / kThreads;
+    static constexpr int dc(int u) { return WIDE ? (u * kThreads) % CF::C : 0; }
+    static constexpr int dt(int u) { return WIDE ? (u * kThreads) / CF::C : u * (kThreads / CF::C); }
+    static constexpr int goff(int u) { return dc(u) + (dt(u) << kRowLog); }   // from the first element
+    int c0, t0, xr;
+    __device__ explicit TileShare(int tx)
+        : c0(WIDE ? tx : tx % CF::C), t0(WIDE ? 0 : tx / CF::C), xr((c0 * CF::MUL) & 31)
+    {
+    }
+    __device__ int rel0() const { return c0 + (t0 << kRowLog); }
+    // Shared-memory word of element u relative to the thread's column base
+    // (the same word ColLayout gives for that column and row).
+    __device__ int soff(int u) const
+    {
+        const int t = t0 + dt(u);
+        return dc(u) * CF::STRIDE + ((CF::SW ? swz(t) : t) ^ xr);
+    }
+};
+
+// Elements of a product from the thread's first element (o0 + rel0) to the
+// end of a length-len array, clamped to [-1, 2^30].
+__device__ __forceinline__ int room_of(size_t len, size_t first)
+{
+    if (len <= first) return -1;
+    const size_t r = len - first;
+    return r > (size_t{1} << 30) ? (1 << 30) : static_cast<int>(r);
+}
+
 template <int K1, bool INV>
 __device__ __forceinline__ void col_tile(uint32_t *smem, const Prod &P, const PrimeInfo &pr, uint32_t tile)
 {
     using CF = ColTile<K1>;
+    using TS = TileShare<CF>;
     constexpr int NP = Sched<K1>::kPasses;
     constexpr int NARR = INV ? 1 : 2;
     const size_t n = size_t{1} << P.k;
     const size_t o0 = static_cast<size_t>(tile) * CF::C;
     const Mod md{pr.p, pr.pp};
+    const TS ts(threadIdx.x);
+    const size_t first = o0 + ts.rel0();
     auto col = [&](int a, int c) {
         return ColLayout<CF::SW>{smem + a * CF::WORDS + c * CF::STRIDE, (c * CF::MUL) & 31};
     };
+    // Tile loads: one cp.async per element (zero-filled past the operand's
+    // end), so all of a thread's loads are in flight together; then each
+    // thread scales the b elements it copied (b N^-1 R^2 R^-1).
 #pragma unroll
     for (int a = 0; a < NARR; a++) {
-        const uint32_t *src = INV ? P.ws : (a ? P.b : P.a);
-        const size_t slen = INV ? n : (a ? P.lb : P.la);
-        for (int i = threadIdx.x; i < CF::C * CF::N1; i += kThreads) {
-            const int t = i / CF::C, c = i % CF::C;
-            const size_t j = o0 + c + (static_cast<size_t>(t) << kRowLog);
-            uint32_t v = j < slen ? __ldg(src + j) : 0u;
-            if (!INV && a == 1) v = mont_mul(v, P.k_scale, pr.p, pr.pp);
-            col(a, c)[t] = v;
+        const uint32_t *base = INV ? P.ws : (a ? P.b : P.a);
+        const int room = room_of(INV ? n : (a ? P.lb : P.la), first);
+        const uint32_t *src = base + first;
+        uint32_t *sm = smem + a * CF::WORDS + ts.c0 * CF::STRIDE;
+#pragma unroll 8
+        for (int u = 0; u < TS::PER; u++) {
+            const bool in = TS::goff(u) < room;
+            cp_async4(sm + ts.soff(u), in ? src + TS::goff(u) : base, in ? 4u : 0u);
         }
+    }
+    cp_async_wait_all();
+    if constexpr (!INV) {
+        uint32_t *sm = smem + CF::WORDS + ts.c0 * CF::STRIDE;
+#pragma unroll 8
+        for (int u = 0; u < TS::PER; u++) sm[ts.soff(u)] = mont_mul(sm[ts.soff(u)], P.k_scale, pr.p, pr.pp);
     }
     __syncthreads();
     const int tid = threadIdx.x % CF::NT1;
@@ -133,12 +185,78 @@ __device__ __forceinline__ void col_tile(uint32_t *smem, const Prod &P, const Pr
     }
 #pragma unroll
     for (int a = 0; a < NARR; a++) {
-        uint32_t *dst = INV ? P.c : P.ws + a * n;
-        const size_t dlen = INV ? P.lc : n;
-        for (int i = threadIdx.x; i < CF::C * CF::N1; i += kThreads) {
-            const int t = i / CF::C, cc = i % CF::C;
-            const size_t j = o0 + cc + (static_cast<size_t>(t) << kRowLog);
-            if (j < dlen) dst[j] = col(a, cc)[t];
+        uint32_t *dst = (INV ? P.c : P.ws + a * n) + first;
+        const int room = INV ? room_of(P.lc, first) : (1 << 30);
+        const uint32_t *sm = smem + a * CF::WORDS + ts.c0 * CF::STRIDE;
+#pragma unroll 8
+        for (int u = 0; u < TS::PER; u++)
+            if (TS::goff(u) < room) dst[TS::goff(u)] = sm[ts.soff(u)];
+    }
+}
+
+// Columns per job for the register column jobs: 2^14 elements per operand.
+constexpr int reg_cols(int k1) { return (1 << 14) >> k1 < (1 << kRowLog) ? (1 << 14) >> k1 : (1 << kRowLog); }
+
+// Column levels 0 .. K1-1 (K1 <= 4) of reg_cols(K1) consecutive columns of
+// one product, in registers: thread tx takes columns o0 + tx + 256 m, G at a
+// time (G x 2^K1 <= 16 elements per operand), element t of column c being
+// word c + (t << kRowLog).  A warp's load or store of one (column, row) slot
+// covers 32 consecutive words, and all of a thread's loads of a step are
+// independent, so they are in flight together.  The columns of a step share
+// their twiddles (levels 0 .. K1-1, block 0 of the transform), so they run
+// as the NARR arrays of one register group.
+template <int K1, bool INV>
+__device__ __forceinline__ void col_regs(const Prod &P, const PrimeInfo &pr, uint32_t tile)
+{
+    constexpr int N1 = 1 << K1, G = 16 / N1, STEPS = reg_cols(K1) / kThreads / G;
+    constexpr int NA = INV ? G : 2 * G;
+    static_assert(STEPS >= 1 && reg_cols(K1) % (kThreads * G) == 0, "register column job geometry");
+    const size_t n = size_t{1} << P.k;
+    const Mod md{pr.p, pr.pp};
+    const size_t c0 = static_cast<size_t>(tile) * reg_cols(K1) + threadIdx.x;
+#pragma unroll 1
+    for (int st = 0; st < STEPS; st++) {
+        const size_t cs = c0 + static_cast<size_t>(st) * G * kThreads;
+        uint32_t x[NA][N1];
+        if constexpr (!INV) {
+#pragma unroll
+            for (int a = 0; a < 2; a++) {
+                const uint32_t *src = a ? P.b : P.a;
+                const size_t len = a ? P.lb : P.la;
+#pragma unroll
+                for (int g = 0; g < G; g++)
+#pragma unroll
+                    for (int t = 0; t < N1; t++) {
+                        const size_t j = cs + g * kThreads + (static_cast<size_t>(t) << kRowLog);
+                        x[a * G + g][t] = j < len ? __ldg(src + j) : 0u;
+                    }
+            }
+#pragma unroll
+            for (int g = 0; g < G; g++)
+#pragma unroll
+                for (int t = 0; t < N1; t++) x[G + g][t] = mont_mul(x[G + g][t], P.k_scale, pr.p, pr.pp);
+            ct_group<K1, NA, true>(x, pr.tw, 0, 0, md);
+#pragma unroll
+            for (int a = 0; a < 2; a++)
+#pragma unroll
+                for (int g = 0; g < G; g++)
+#pragma unroll
+                    for (int t = 0; t < N1; t++)
+                        P.ws[a * n + cs + g * kThreads + (static_cast<size_t>(t) << kRowLog)] = x[a * G + g][t];
+        } else {
+#pragma unroll
+            for (int g = 0; g < G; g++)
+#pragma unroll
+                for (int t = 0; t < N1; t++)
+                    x[g][t] = P.ws[cs + g * kThreads + (static_cast<size_t>(t) << kRowLog)];
+            gs_group<K1, NA, true>(x, pr.itw, 0, 0, md);
+#pragma unroll
+            for (int g = 0; g < G; g++)
+#pragma unroll
+                for (int t = 0; t < N1; t++) {
+                    const size_t j = cs + g * kThreads + (static_cast<size_t>(t) << kRowLog);
+                    if (j < P.lc) P.c[j] = x[g][t];
+                }
         }
     }
 }
@@ -147,14 +265,14 @@ template <bool INV>
 __device__ __forceinline__ void col_job(uint32_t *smem, const Prod &P, const PrimeInfo &pr, uint32_t tile)
 {
     switch (P.k - kRowLog) {
-    case 2: col_tile<2, INV>(smem, P, pr, tile); break;
-    case 3: col_tile<3, INV>(smem, P, pr, tile); break;
-    case 4: col_tile<4, INV>(smem, P, pr, tile); break;
+    case 1: col_regs<1, INV>(P, pr, tile); break;
+    case 2: col_regs<2, INV>(P, pr, tile); break;
+    case 3: col_regs<3, INV>(P, pr, tile); break;
+    case 4: col_regs<4, INV>(P, pr, tile); break;
     case 5: col_tile<5, INV>(smem, P, pr, tile); break;
     case 6: col_tile<6, INV>(smem, P, pr, tile); break;
     case 7: col_tile<7, INV>(smem, P, pr, tile); break;
     case 8: col_tile<8, INV>(smem, P, pr, tile); break;
-    case 9: col_tile<9, INV>(smem, P, pr, tile); break;
     default: break;
     }
 }
@@ -203,8 +321,17 @@ __global__ void __launch_bounds__(kThreads, MINB) k_polymul_batch(BatchArgs A)
     __shared__ uint32_t s_job;
     __shared__ int s_ok;
     uint32_t *err = A.sync + 1;
+    // Thread 0 claims one job ahead: the claim of a CTA's next job is issued
+    // when its current job starts, so the atomic's round trip overlaps the
+    // work.  Progress still holds: every job waits only on earlier jobs, a
+    // CTA finishes its current job before its next, so the earliest
+    // unfinished job is always some CTA's current job and can run.
+    uint32_t next = 0;
+    if (threadIdx.x == 0) {
+        s_job = atomicAdd(A.sync, 1u);
+        next = atomicAdd(A.sync, 1u);
+    }
     for (;;) {
-        if (threadIdx.x == 0) s_job = atomicAdd(A.sync, 1u);
         __syncthreads();
         const uint32_t jid = s_job;
         if (jid >= A.njobs) break;
@@ -231,7 +358,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_polymul_batch(BatchArgs A)
                 } else if (J.type == JOB_ROW) {
                     uint32_t *row = P.ws + (static_cast<size_t>(J.idx) << kRowLog);
                     const size_t n = size_t{1} << P.k;
-                    polymul_team<kRowLog, false, false>(smem, threadIdx.x, row, size_t{1} << kRowLog, row + n,
+                    polymul_team<kRowLog, false, false, kThreads>(smem, threadIdx.x, row, size_t{1} << kRowLog, row + n,
                                                         size_t{1} << kRowLog, row, size_t{1} << kRowLog, pr.tw,
                                                         pr.itw, static_cast<int>(P.k) - kRowLog,
                                                         static_cast<int>(J.idx), pr.p, pr.pp, 0u);
@@ -246,12 +373,16 @@ __global__ void __launch_bounds__(kThreads, MINB) k_polymul_batch(BatchArgs A)
             }
         }
         __syncthreads();
+        if (threadIdx.x == 0) {
+            s_job = next;
+            next = atomicAdd(A.sync, 1u);
+        }
     }
 }
 
 int col_tiles(int k1)
 {
-    return (1 << kRowLog) / col_tile_cols(k1);
+    return (1 << kRowLog) / (k1 <= kMaxRegColLog ? reg_cols(k1) : col_tile_cols(k1));
 }
 
 int teams_for(int k)
