@@ -53,8 +53,9 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--log2n", type=int, default=28, help="elements per operand (default 2^28)")
-    ap.add_argument("--sections", default="uniform,uneven,serve",
-                    help="extra polymul sections to run (comma list of uniform, uneven, serve; empty for none)")
+    ap.add_argument("--sections", default="uniform,reductions,uneven,serve",
+                    help="extra polymul sections to run (comma list of uniform, reductions, uneven, serve; "
+                         "empty for none)")
     ap.add_argument("--no-per-product", action="store_true",
                     help="skip the one-launch-per-product comparison of the uneven batch")
     return ap.parse_args()
@@ -353,6 +354,8 @@ def run_gpu(args, ws, rank, local):
         sampler2.start()
         if "uniform" in secs:
             extra["polymul_uniform_4096x2048"] = bp.uniform_batch(m, torch, peaks, cpu=not args.no_cpu_baseline)
+        if "reductions" in secs:
+            extra["polymul_alg2_vs_alg3_4096x2048"] = bp.reduction_ab(m, torch)
         if "uneven" in secs:
             extra["polymul_uneven_10000"] = bp.uneven_batch(m, torch, peaks, cpu=not args.no_cpu_baseline,
                                                             per_product=not args.no_per_product)

@@ -83,7 +83,7 @@ def uniform_batch(m, torch, peaks, steps=20, warmup=3, cpu=True):
     res = {"workload": "4096 products, la = lb = 2048, P = 2013265921, N = 4096 (one fused kernel)",
            "value": coeffs / ms / 1e6, "unit": "Gcoef/s", "ms": ms, "steps": steps, "warmup": warmup,
            "l2": "flushed (256 MiB write) before every timed launch", "gpu_launches": steps,
-           "roofline": {"bound": "alu", "kernel": "k_polymul<12>", "achieved": ops / (ms / 1e3) / 1e12,
+           "roofline": {"bound": "alu", "kernel": "k_polymul<12, RedAlg2>", "achieved": ops / (ms / 1e3) / 1e12,
                         "peak": peak / 1e12, "unit": "Tops/s (integer lane-ops)", "frac": ops / (ms / 1e3) / peak,
                         "peak_source": "derived: 152 SMs x 128 int lanes/clk x %.0f MHz" % peaks["sm_max_mhz"],
                         "algorithmic_ops": ops, "traffic": None},
@@ -103,6 +103,49 @@ def uniform_batch(m, torch, peaks, steps=20, warmup=3, cpu=True):
         t = time.perf_counter() - t0
         res["cpu_baseline"] = {"value": coeffs / t / 1e9, "unit": "Gcoef/s", "cores": oracle.num_threads(),
                                "kind": "oracle", "sample": "all 4096 products (oracle radix-2 NTT, OpenMP over products)"}
+    del flush
+    return res
+
+
+def reduction_ab(m, torch, steps=20, warmup=3):
+    """Alg. 2 (REDC) against Alg. 3 (FourierREDC) as the twiddle, scaling and
+    pointwise multiply of the same fused kernels: 4096 products of
+    length-2048 polynomials mod P2 = 469762049 (Alg. 3 needs P < 2^30), L2
+    flushed before every launch, launches alternating between the two."""
+    import oracle
+    p, a, b = synth.batch_uniform(p=synth.P2)
+    count, L = a.shape
+    da = torch.from_numpy(a.view(np.int32)).cuda()
+    db = torch.from_numpy(b.view(np.int32)).cuda()
+    out = {k: torch.empty((count, 2 * L - 1), dtype=torch.int32, device="cuda") for k in ("alg2", "alg3")}
+    fns = {"alg2": m.polymul_many, "alg3": m.polymul_many_fourier}
+    flush = torch.empty(64 << 20, dtype=torch.int32, device="cuda")
+    for _ in range(warmup):
+        for k, f in fns.items():
+            f(p, da, db, out=out[k])
+    torch.cuda.synchronize()
+    evs = {k: [] for k in fns}
+    for _ in range(steps):
+        for k, f in fns.items():
+            flush.fill_(1)
+            e0, e1 = _events(torch)
+            e0.record()
+            f(p, da, db, out=out[k])
+            e1.record()
+            evs[k].append((e0, e1))
+    torch.cuda.synchronize()
+    assert torch.equal(out["alg2"], out["alg3"]), "Alg. 2 and Alg. 3 products differ"
+    got = out["alg3"][:2].cpu().numpy().view(np.uint32)
+    for i in range(2):
+        assert np.array_equal(got[i], oracle.polymul_ntt(p, a[i], b[i])), "Alg. 3 parity spot check failed"
+    res = {"workload": "4096 products, la = lb = 2048, P = 469762049, N = 4096 (one fused kernel each)",
+           "unit": "Gcoef/s", "steps": steps, "warmup": warmup, "l2": "flushed (256 MiB write) before every launch",
+           "gpu_launches": 2 * steps}
+    for k in fns:
+        ms = float(np.mean([e0.elapsed_time(e1) for e0, e1 in evs[k]]))
+        res[k] = {"ms": ms, "value": count * 2 * L / ms / 1e6,
+                  "kernel": "k_polymul<12, %s>" % ("RedAlg2" if k == "alg2" else "RedAlg3")}
+    res["alg3_over_alg2_time"] = res["alg3"]["ms"] / res["alg2"]["ms"]
     del flush
     return res
 

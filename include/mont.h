@@ -159,6 +159,15 @@ int polymul(uint32_t p, const uint32_t *a, size_t la, const uint32_t *b, size_t 
 int polymul_many(uint32_t p, const uint32_t *a, size_t la, const uint32_t *b, size_t lb, uint32_t *c,
                  size_t count, cudaStream_t stream);
 
+/* polymul_many with Alg. 3 (FourierREDC, Sec. 3.1) in place of Alg. 2 for
+ * every twiddle, scaling and pointwise multiply of the same fused kernels.
+ * Same layout and results (bit for bit) as polymul_many; for comparing the
+ * two reductions.  p must be a Fourier prime c 2^n + 1 with 2n >= 32 and
+ * p < 2^30 (Alg. 3's 31-bit sign tests), else MONT_ERANGE; N <= 2^14 only,
+ * else MONT_EUNSUPPORTED; other errors as polymul_many. */
+int polymul_many_fourier(uint32_t p, const uint32_t *a, size_t la, const uint32_t *b, size_t lb, uint32_t *c,
+                         size_t count, cudaStream_t stream);
+
 /* Scratch bytes polymul_many_ws needs for `count` products of this shape
  * (0 when N <= 2^14). */
 size_t polymul_workspace_bytes(size_t la, size_t lb, size_t count);

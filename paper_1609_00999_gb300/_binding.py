@@ -87,6 +87,8 @@ def _declare_ntt(L):
     L.polymul.restype = ctypes.c_int
     L.polymul_many.argtypes = [ctypes.c_uint32, _vp, _sz, _vp, _sz, _vp, _sz, _vp]
     L.polymul_many.restype = ctypes.c_int
+    L.polymul_many_fourier.argtypes = [ctypes.c_uint32, _vp, _sz, _vp, _sz, _vp, _sz, _vp]
+    L.polymul_many_fourier.restype = ctypes.c_int
     L.polymul_many_ws.argtypes = [ctypes.c_uint32, _vp, _sz, _vp, _sz, _vp, _sz, _vp, _sz, _vp]
     L.polymul_many_ws.restype = ctypes.c_int
     L.polymul_workspace_bytes.argtypes = [_sz, _sz, _sz]
@@ -349,6 +351,23 @@ def polymul_many(p, a, b, out=None, stream=None):
         raise ValueError("out must have %d elements" % (count * lc))
     _check(lib().polymul_many(int(p), _dev_ptr(a, "a"), la, _dev_ptr(b, "b"), lb, _dev_ptr(out, "out"), count,
                               _stream_handle(stream, a.device)), "polymul_many")
+    return out
+
+
+def polymul_many_fourier(p, a, b, out=None, stream=None):
+    """polymul_many with the FourierREDC (Alg. 3) twiddle multiply: Fourier
+    primes below 2^30 with 2n >= 32, N <= 2^14; identical results."""
+    if a.dim() != 2 or b.dim() != 2 or a.shape[0] != b.shape[0]:
+        raise ValueError("a and b must be [count][la] and [count][lb]")
+    count, la = a.shape
+    lb = b.shape[1]
+    lc = la + lb - 1
+    if out is None:
+        out = torch.empty((count, lc), dtype=a.dtype, device=a.device)
+    elif out.numel() != count * lc:
+        raise ValueError("out must have %d elements" % (count * lc))
+    _check(lib().polymul_many_fourier(int(p), _dev_ptr(a, "a"), la, _dev_ptr(b, "b"), lb, _dev_ptr(out, "out"),
+                                      count, _stream_handle(stream, a.device)), "polymul_many_fourier")
     return out
 
 

@@ -37,25 +37,6 @@ __device__ __forceinline__ uint32_t barrett(uint32_t a, uint32_t b, uint32_t p, 
     return static_cast<uint32_t>(t);
 }
 
-// Alg. 3 (Montgomery over the Fourier prime P = c 2^n + 1, R = 2^32, 2n >= 32):
-// q1 = ab / R, r1 = ab mod R, (q2, r2) = (c 2^n r1) / R, mod R,
-// q3 = (c 2^n r2) / R, t = q1 - q2 + q3 in (-(P-1), 2(P-1)), then the
-// sign-mask corrections.  The 31-bit sign tests need 2(P-1) < 2^31, i.e.
-// P < 2^30 (the host rejects larger P).  Result: ab R^-1 mod P, as REDC.
-__device__ __forceinline__ uint32_t fourier_redc(uint32_t a, uint32_t b, uint32_t p, uint32_t w)
-{
-    const uint64_t T = static_cast<uint64_t>(a) * b;
-    const uint32_t q1 = static_cast<uint32_t>(T >> 32), r1 = static_cast<uint32_t>(T);
-    const uint64_t U = static_cast<uint64_t>(r1) * w;
-    const uint32_t q2 = static_cast<uint32_t>(U >> 32), r2 = static_cast<uint32_t>(U);
-    const uint32_t q3 = __umulhi(r2, w);
-    int32_t t = static_cast<int32_t>(q1 - q2 + q3);
-    t += (t >> 31) & static_cast<int32_t>(p);
-    t -= static_cast<int32_t>(p);
-    t += (t >> 31) & static_cast<int32_t>(p);
-    return static_cast<uint32_t>(t);
-}
-
 constexpr int kThreads = 256;
 constexpr int kIlp = 2;
 

@@ -37,23 +37,6 @@ __device__ __forceinline__ int brev(int k)
     else return static_cast<int>(__brev(static_cast<unsigned>(k)) >> (32 - LOGN));
 }
 
-template <int LOGN>
-__global__ void __launch_bounds__(teams_of<LOGN>() * nt_of<LOGN>(), min_ctas_of<LOGN>())
-k_polymul(PolyArgs A)
-{
-    constexpr int NT = nt_of<LOGN>();
-    extern __shared__ __align__(16) uint32_t smem[];
-    const int team = threadIdx.x / NT, tid = threadIdx.x - team * NT;
-    const size_t prod = static_cast<size_t>(blockIdx.x) * teams_of<LOGN>() + team;
-    const bool valid = prod < A.count;
-    const uint32_t *ga = A.a + (valid ? prod * A.la : 0);
-    const uint32_t *gb = A.b + (valid ? prod * A.lb : 0);
-    uint32_t *gc = A.c + (valid ? prod * A.lc : 0);
-    uint32_t *sm = smem + static_cast<size_t>(team) * team_smem_words<LOGN>();
-    polymul_team<LOGN, true, true>(sm, tid, ga, valid ? A.la : 0, gb, valid ? A.lb : 0, gc, valid ? A.lc : 0,
-                                   A.tw, A.itw, 0, 0, A.p, A.pp, A.k_scale);
-}
-
 struct NttArgs {
     uint32_t *data;
     size_t batch;
@@ -100,18 +83,6 @@ k_ntt_inv(NttArgs A)
     inv_passes<LOGN, NT, true, NP - 1, 0>(lay, tid, A.tw, 0, 0, Mod{A.p, A.pp});
     if (valid)
         for (int k = tid; k < N; k += NT) g[k] = mont_mul(lay[k], A.ninv_mont, A.p, A.pp);
-}
-
-template <int LOGN>
-int launch_polymul_smem(const PolyArgs &A, cudaStream_t s)
-{
-    constexpr int T = teams_of<LOGN>(), NT = nt_of<LOGN>();
-    const size_t smem = static_cast<size_t>(T) * team_smem_words<LOGN>() * sizeof(uint32_t);
-    if (ensure_smem(k_polymul<LOGN>, smem) != MONT_OK) return MONT_ECUDA;
-    const size_t grid = (A.count + T - 1) / T;
-    if (grid > 0x7FFFFFFFu) return MONT_ERANGE;
-    k_polymul<LOGN><<<static_cast<unsigned>(grid), T * NT, smem, s>>>(A);
-    return launch_status();
 }
 
 template <int LOGN>
@@ -173,7 +144,7 @@ int dispatch_polymul_smem(int log2n, const PolyArgs &A, cudaStream_t s)
 {
     switch (log2n) {
 #define X(L) \
-    case L: return launch_polymul_smem<L>(A, s);
+    case L: return launch_polymul_smem<L, RedAlg2>(A, s);
         MONT_LOGN_CASES(X)
 #undef X
     default: return MONT_EUNSUPPORTED;

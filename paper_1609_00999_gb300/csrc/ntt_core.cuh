@@ -35,6 +35,22 @@ struct Mod {
     uint32_t pp;   // P' = -P^-1 mod 2^32
 };
 
+// Reduction policies for the twiddle and pointwise multiplies: mul(a, b)
+// returns a b R^-1 mod P in [0, P) for a < 2P, b < P.  RedAlg2 is REDC
+// (Alg. 2) and serves every P < 2^31; RedAlg3 is FourierREDC (Alg. 3) for
+// Fourier primes P = c 2^n + 1 < 2^30 with 2n >= 32.  Both give the same
+// residue, so tables and results do not depend on the policy.
+struct RedAlg2 {
+    __device__ __forceinline__ static uint32_t mul(uint32_t a, uint32_t b, Mod m) { return mont_mul(a, b, m.p, m.pp); }
+};
+
+struct RedAlg3 {
+    __device__ __forceinline__ static uint32_t mul(uint32_t a, uint32_t b, Mod m)
+    {
+        return fourier_redc(a, b, m.p, m.p - 1u);
+    }
+};
+
 // Forward values are kept lazily in [0, 2P): with P < 2^31, 2P < R, so the
 // sum of two reduced values fits 32 bits, and REDC of a lazy value by a
 // reduced twiddle (T < 2P^2 < RP) is below 2P.  Each CT butterfly therefore
@@ -46,9 +62,10 @@ struct Mod {
 // in [0, P).
 
 // CT butterfly: x, y in [0, 2P) -> x + r y, x - r y in [0, 2P).
+template <class RED>
 __device__ __forceinline__ void bfly_ct(uint32_t &x, uint32_t &y, uint32_t w, Mod m)
 {
-    const uint32_t t = csub(redc_lazy(y, w, m.p, m.pp), m.p);
+    const uint32_t t = RED::mul(y, w, m);
     const uint32_t u = csub(x, m.p);
     x = u + t;
     y = u - t + m.p;
@@ -82,12 +99,13 @@ __device__ __forceinline__ void bfly_gs_one(uint32_t &x, uint32_t &y, Mod m)
 
 // GS butterfly, all values in [0, P).  x - y + P < 2P is a valid REDC operand
 // (one factor < 2P, the other < P keeps T < RP), so it is not reduced first.
+template <class RED>
 __device__ __forceinline__ void bfly_gs(uint32_t &x, uint32_t &y, uint32_t w, Mod m)
 {
     const uint32_t s = x + y;
     const uint32_t d = x - y + m.p;
     x = csub(s, m.p);
-    y = csub(redc_lazy(d, w, m.p, m.pp), m.p);
+    y = RED::mul(d, w, m);
 }
 
 __device__ __forceinline__ int swz(int j)
@@ -123,7 +141,7 @@ __device__ __forceinline__ void load_tw(uint32_t (&w)[CNT], const uint32_t *__re
 // FIRST_BLOCK: the group lies in block 0 of the transform at every level
 // (blk == 0 and s_abs == 0), so local block 0 has twiddle 1, and local
 // level 0 is level 0 of the transform (reduced inputs).
-template <int E, int L, int NARR, bool FIRST_BLOCK>
+template <int E, int L, int NARR, bool FIRST_BLOCK, class RED>
 __device__ __forceinline__ void ct_level(uint32_t (&x)[NARR][1 << E], const uint32_t *__restrict__ tw, int s_abs,
                                          int blk, Mod m)
 {
@@ -142,12 +160,12 @@ __device__ __forceinline__ void ct_level(uint32_t (&x)[NARR][1 << E], const uint
                     if constexpr (L == 0) bfly_ct_first(x0, x1, m);
                     else bfly_ct_one(x0, x1, m);
                 } else {
-                    bfly_ct(x0, x1, w[lb], m);
+                    bfly_ct<RED>(x0, x1, w[lb], m);
                 }
             }
 }
 
-template <int E, int L, int NARR, bool FIRST_BLOCK>
+template <int E, int L, int NARR, bool FIRST_BLOCK, class RED>
 __device__ __forceinline__ void gs_level(uint32_t (&x)[NARR][1 << E], const uint32_t *__restrict__ itw, int s_abs,
                                          int blk, Mod m)
 {
@@ -163,30 +181,30 @@ __device__ __forceinline__ void gs_level(uint32_t (&x)[NARR][1 << E], const uint
                 uint32_t &x0 = x[a][lb * 2 * HALF + u];
                 uint32_t &x1 = x[a][lb * 2 * HALF + u + HALF];
                 if (FIRST_BLOCK && lb == 0) bfly_gs_one(x0, x1, m);
-                else bfly_gs(x0, x1, w[lb], m);
+                else bfly_gs<RED>(x0, x1, w[lb], m);
             }
 }
 
 // Forward levels s_abs .. s_abs+E-1 on NARR register groups of 2^E elements
 // sharing block index `blk`.
-template <int E, int NARR, bool FIRST_BLOCK, int L = 0>
+template <int E, int NARR, bool FIRST_BLOCK, class RED = RedAlg2, int L = 0>
 __device__ __forceinline__ void ct_group(uint32_t (&x)[NARR][1 << E], const uint32_t *__restrict__ tw, int s_abs,
                                          int blk, Mod m)
 {
     if constexpr (L < E) {
-        ct_level<E, L, NARR, FIRST_BLOCK>(x, tw, s_abs, blk, m);
-        ct_group<E, NARR, FIRST_BLOCK, L + 1>(x, tw, s_abs, blk, m);
+        ct_level<E, L, NARR, FIRST_BLOCK, RED>(x, tw, s_abs, blk, m);
+        ct_group<E, NARR, FIRST_BLOCK, RED, L + 1>(x, tw, s_abs, blk, m);
     }
 }
 
 // Inverse levels s_abs+E-1 .. s_abs (reverse order), same grouping.
-template <int E, int NARR, bool FIRST_BLOCK, int L = E - 1>
+template <int E, int NARR, bool FIRST_BLOCK, class RED = RedAlg2, int L = E - 1>
 __device__ __forceinline__ void gs_group(uint32_t (&x)[NARR][1 << E], const uint32_t *__restrict__ itw, int s_abs,
                                          int blk, Mod m)
 {
     if constexpr (L >= 0) {
-        gs_level<E, L, NARR, FIRST_BLOCK>(x, itw, s_abs, blk, m);
-        gs_group<E, NARR, FIRST_BLOCK, L - 1>(x, itw, s_abs, blk, m);
+        gs_level<E, L, NARR, FIRST_BLOCK, RED>(x, itw, s_abs, blk, m);
+        gs_group<E, NARR, FIRST_BLOCK, RED, L - 1>(x, itw, s_abs, blk, m);
     }
 }
 
@@ -276,7 +294,7 @@ struct ColLayout {
 
 // The NARR arrays are transformed one after the other (the twiddles are
 // reloaded from L1 for each), which keeps one group live at a time.
-template <int LOGN, int NT, int I, int NARR, bool BASE0, class L>
+template <int LOGN, int NT, int I, int NARR, bool BASE0, class RED = RedAlg2, class L>
 __device__ __forceinline__ void fwd_pass(const L (&lay)[NARR], int tid, const uint32_t *__restrict__ tw, int s_base,
                                          int b, Mod m)
 {
@@ -289,13 +307,13 @@ __device__ __forceinline__ void fwd_pass(const L (&lay)[NARR], int tid, const ui
             uint32_t x[1][PG::G];
 #pragma unroll
             for (int t = 0; t < PG::G; t++) x[0][t] = elem(lay[a], base, t * PG::HMIN);
-            ct_group<PG::E, 1, BASE0 && PG::S0 == 0>(x, tw, s_base + PG::S0, (b << PG::S0) + blk, m);
+            ct_group<PG::E, 1, BASE0 && PG::S0 == 0, RED>(x, tw, s_base + PG::S0, (b << PG::S0) + blk, m);
 #pragma unroll
             for (int t = 0; t < PG::G; t++) elem(lay[a], base, t * PG::HMIN) = x[0][t];
         }
 }
 
-template <int LOGN, int NT, int I, bool BASE0, class L>
+template <int LOGN, int NT, int I, bool BASE0, class RED = RedAlg2, class L>
 __device__ __forceinline__ void inv_pass(const L &lay, int tid, const uint32_t *__restrict__ itw, int s_base, int b,
                                          Mod m)
 {
@@ -306,40 +324,40 @@ __device__ __forceinline__ void inv_pass(const L &lay, int tid, const uint32_t *
         uint32_t x[1][PG::G];
 #pragma unroll
         for (int t = 0; t < PG::G; t++) x[0][t] = elem(lay, base, t * PG::HMIN);
-        gs_group<PG::E, 1, BASE0 && PG::S0 == 0>(x, itw, s_base + PG::S0, (b << PG::S0) + blk, m);
+        gs_group<PG::E, 1, BASE0 && PG::S0 == 0, RED>(x, itw, s_base + PG::S0, (b << PG::S0) + blk, m);
 #pragma unroll
         for (int t = 0; t < PG::G; t++) elem(lay, base, t * PG::HMIN) = x[0][t];
     }
 }
 
 // Forward passes I .. LAST, each followed by a CTA barrier.
-template <int LOGN, int NT, int NARR, bool BASE0, int I, int LAST, class L>
+template <int LOGN, int NT, int NARR, bool BASE0, int I, int LAST, class RED = RedAlg2, class L>
 __device__ __forceinline__ void fwd_passes(const L (&lay)[NARR], int tid, const uint32_t *__restrict__ tw,
                                            int s_base, int b, Mod m)
 {
     if constexpr (I <= LAST) {
-        fwd_pass<LOGN, NT, I, NARR, BASE0>(lay, tid, tw, s_base, b, m);
+        fwd_pass<LOGN, NT, I, NARR, BASE0, RED>(lay, tid, tw, s_base, b, m);
         __syncthreads();
-        fwd_passes<LOGN, NT, NARR, BASE0, I + 1, LAST>(lay, tid, tw, s_base, b, m);
+        fwd_passes<LOGN, NT, NARR, BASE0, I + 1, LAST, RED>(lay, tid, tw, s_base, b, m);
     }
 }
 
 // Inverse passes I, I-1, .. FIRST, each followed by a CTA barrier.
-template <int LOGN, int NT, bool BASE0, int I, int FIRST, class L>
+template <int LOGN, int NT, bool BASE0, int I, int FIRST, class RED = RedAlg2, class L>
 __device__ __forceinline__ void inv_passes(const L &lay, int tid, const uint32_t *__restrict__ itw, int s_base, int b,
                                            Mod m)
 {
     if constexpr (I >= FIRST) {
-        inv_pass<LOGN, NT, I, BASE0>(lay, tid, itw, s_base, b, m);
+        inv_pass<LOGN, NT, I, BASE0, RED>(lay, tid, itw, s_base, b, m);
         __syncthreads();
-        inv_passes<LOGN, NT, BASE0, I - 1, FIRST>(lay, tid, itw, s_base, b, m);
+        inv_passes<LOGN, NT, BASE0, I - 1, FIRST, RED>(lay, tid, itw, s_base, b, m);
     }
 }
 
 // Last forward pass of both operands, pointwise REDC product (A B~ R^-1, one
 // lazy factor reduced first),
 // then the same levels of the inverse in reverse, result into lay[0].
-template <int LOGN, int NT, bool BASE0, class L>
+template <int LOGN, int NT, bool BASE0, class RED = RedAlg2, class L>
 __device__ __forceinline__ void fused_middle_pass(const L (&lay)[2], int tid, const uint32_t *__restrict__ tw,
                                                   const uint32_t *__restrict__ itw, int s_base, int b, Mod m)
 {
@@ -353,11 +371,11 @@ __device__ __forceinline__ void fused_middle_pass(const L (&lay)[2], int tid, co
             x[0][t] = elem(lay[0], base, t * PL::HMIN);
             x[1][t] = elem(lay[1], base, t * PL::HMIN);
         }
-        ct_group<PL::E, 2, BASE0 && PL::S0 == 0>(x, tw, s_base + PL::S0, blk, m);
+        ct_group<PL::E, 2, BASE0 && PL::S0 == 0, RED>(x, tw, s_base + PL::S0, blk, m);
         uint32_t y[1][PL::G];
 #pragma unroll
-        for (int t = 0; t < PL::G; t++) y[0][t] = mont_mul(csub(x[0][t], m.p), x[1][t], m.p, m.pp);
-        gs_group<PL::E, 1, BASE0 && PL::S0 == 0>(y, itw, s_base + PL::S0, blk, m);
+        for (int t = 0; t < PL::G; t++) y[0][t] = RED::mul(csub(x[0][t], m.p), x[1][t], m);
+        gs_group<PL::E, 1, BASE0 && PL::S0 == 0, RED>(y, itw, s_base + PL::S0, blk, m);
 #pragma unroll
         for (int t = 0; t < PL::G; t++) elem(lay[0], base, t * PL::HMIN) = y[0][t];
     }

@@ -83,7 +83,7 @@ int ensure_smem(K kernel, size_t bytes)
 // Reads of a and b (lengths la, lb, zero beyond) all happen before the first
 // barrier, so gc may alias ga (in-place row passes).  Every thread of the CTA
 // must call it (it contains __syncthreads).  la, lb, lc <= 2^LOGN.
-template <int LOGN, bool BASE0, bool SCALE_B, int NT = nt_of<LOGN>()>
+template <int LOGN, bool BASE0, bool SCALE_B, int NT = nt_of<LOGN>(), class RED = RedAlg2>
 __device__ __forceinline__ void polymul_team(uint32_t *sm, int tid, const uint32_t *ga, size_t la,
                                              const uint32_t *gb, size_t lb, uint32_t *gc, size_t lc,
                                              const uint32_t *__restrict__ tw, const uint32_t *__restrict__ itw, int s_base,
@@ -93,8 +93,8 @@ __device__ __forceinline__ void polymul_team(uint32_t *sm, int tid, const uint32
     const Mod md{p, pp};
     if constexpr (LOGN == 0) {
         if (lc > 0) {
-            const uint32_t bb = SCALE_B ? mont_mul(gb[0], k_scale, p, pp) : gb[0];
-            gc[0] = mont_mul(ga[0], bb, p, pp);
+            const uint32_t bb = SCALE_B ? RED::mul(gb[0], k_scale, md) : gb[0];
+            gc[0] = RED::mul(ga[0], bb, md);
         }
     } else {
         const PadLayout lay[2] = {{sm}, {sm + PadLayout::words(N)}};
@@ -110,13 +110,13 @@ __device__ __forceinline__ void polymul_team(uint32_t *sm, int tid, const uint32
                     const int j = base + t * P0::HMIN;
                     x[0][t] = j < la32 ? __ldg(ga + j) : 0u;
                     const uint32_t bj = j < lb32 ? __ldg(gb + j) : 0u;
-                    x[1][t] = SCALE_B ? mont_mul(bj, k_scale, p, pp) : bj;
+                    x[1][t] = SCALE_B ? RED::mul(bj, k_scale, md) : bj;
                 }
-                ct_group<P0::E, 2, BASE0>(x, tw, s_base, b_idx, md);
+                ct_group<P0::E, 2, BASE0, RED>(x, tw, s_base, b_idx, md);
                 uint32_t y[1][P0::G];
 #pragma unroll
-                for (int t = 0; t < P0::G; t++) y[0][t] = mont_mul(csub(x[0][t], p), x[1][t], p, pp);
-                gs_group<P0::E, 1, BASE0>(y, itw, s_base, b_idx, md);
+                for (int t = 0; t < P0::G; t++) y[0][t] = RED::mul(csub(x[0][t], p), x[1][t], md);
+                gs_group<P0::E, 1, BASE0, RED>(y, itw, s_base, b_idx, md);
 #pragma unroll
                 for (int t = 0; t < P0::G; t++) {
                     const int j = base + t * P0::HMIN;
@@ -136,9 +136,9 @@ __device__ __forceinline__ void polymul_team(uint32_t *sm, int tid, const uint32
                     for (int t = 0; t < P0::G; t++) {
                         const int j = base + t * P0::HMIN;
                         const uint32_t v = j < len ? __ldg(g + j) : 0u;
-                        x[0][t] = (SCALE_B && a) ? mont_mul(v, k_scale, p, pp) : v;
+                        x[0][t] = (SCALE_B && a) ? RED::mul(v, k_scale, md) : v;
                     }
-                    ct_group<P0::E, 1, BASE0>(x, tw, s_base, b_idx, md);
+                    ct_group<P0::E, 1, BASE0, RED>(x, tw, s_base, b_idx, md);
 #pragma unroll
                     for (int t = 0; t < P0::G; t++) elem(lay[a], base, t * P0::HMIN) = x[0][t];
                 }
@@ -146,17 +146,17 @@ __device__ __forceinline__ void polymul_team(uint32_t *sm, int tid, const uint32
         }
         if constexpr (NP > 1) {
             __syncthreads();
-            fwd_passes<LOGN, NT, 2, BASE0, 1, NP - 2>(lay, tid, tw, s_base, b_idx, md);
-            fused_middle_pass<LOGN, NT, BASE0>(lay, tid, tw, itw, s_base, b_idx, md);
+            fwd_passes<LOGN, NT, 2, BASE0, 1, NP - 2, RED>(lay, tid, tw, s_base, b_idx, md);
+            fused_middle_pass<LOGN, NT, BASE0, RED>(lay, tid, tw, itw, s_base, b_idx, md);
             __syncthreads();
-            inv_passes<LOGN, NT, BASE0, NP - 2, 1>(lay[0], tid, itw, s_base, b_idx, md);
+            inv_passes<LOGN, NT, BASE0, NP - 2, 1, RED>(lay[0], tid, itw, s_base, b_idx, md);
 #pragma unroll
             for (int r = 0; r < P0::GPT; r++) {
                 const int base = P0::base(tid, r);
                 uint32_t y[1][P0::G];
 #pragma unroll
                 for (int t = 0; t < P0::G; t++) y[0][t] = elem(lay[0], base, t * P0::HMIN);
-                gs_group<P0::E, 1, BASE0>(y, itw, s_base, b_idx, md);
+                gs_group<P0::E, 1, BASE0, RED>(y, itw, s_base, b_idx, md);
 #pragma unroll
                 for (int t = 0; t < P0::G; t++) {
                     const int j = base + t * P0::HMIN;
@@ -166,6 +166,41 @@ __device__ __forceinline__ void polymul_team(uint32_t *sm, int tid, const uint32
         }
     }
 }
+
+namespace {
+
+// Fused products of N = 2^LOGN <= 2^14: teams_of<LOGN>() products per CTA,
+// one per team, A.count products of [la] x [lb] -> [lc] laid out row-major.
+template <int LOGN, class RED>
+__global__ void __launch_bounds__(teams_of<LOGN>() * nt_of<LOGN>(), min_ctas_of<LOGN>())
+k_polymul(PolyArgs A)
+{
+    constexpr int NT = nt_of<LOGN>();
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int team = threadIdx.x / NT, tid = threadIdx.x - team * NT;
+    const size_t prod = static_cast<size_t>(blockIdx.x) * teams_of<LOGN>() + team;
+    const bool valid = prod < A.count;
+    const uint32_t *ga = A.a + (valid ? prod * A.la : 0);
+    const uint32_t *gb = A.b + (valid ? prod * A.lb : 0);
+    uint32_t *gc = A.c + (valid ? prod * A.lc : 0);
+    uint32_t *sm = smem + static_cast<size_t>(team) * team_smem_words<LOGN>();
+    polymul_team<LOGN, true, true, NT, RED>(sm, tid, ga, valid ? A.la : 0, gb, valid ? A.lb : 0, gc,
+                                            valid ? A.lc : 0, A.tw, A.itw, 0, 0, A.p, A.pp, A.k_scale);
+}
+
+template <int LOGN, class RED>
+int launch_polymul_smem(const PolyArgs &A, cudaStream_t s)
+{
+    constexpr int T = teams_of<LOGN>(), NT = nt_of<LOGN>();
+    const size_t smem = static_cast<size_t>(T) * team_smem_words<LOGN>() * sizeof(uint32_t);
+    if (ensure_smem(k_polymul<LOGN, RED>, smem) != MONT_OK) return MONT_ECUDA;
+    const size_t grid = (A.count + T - 1) / T;
+    if (grid > 0x7FFFFFFFu) return MONT_ERANGE;
+    k_polymul<LOGN, RED><<<static_cast<unsigned>(grid), T * NT, smem, s>>>(A);
+    return launch_status();
+}
+
+}  // namespace
 
 int ceil_log2(size_t n);
 int dispatch_polymul_smem(int log2n, const PolyArgs &A, cudaStream_t s);
