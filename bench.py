@@ -53,6 +53,8 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--log2n", type=int, default=28, help="elements per operand (default 2^28)")
+    ap.add_argument("--batch-config", default=None,
+                    help="uneven section: fixed launch shape CTAS_PER_SM,ORDER,KERNEL instead of autotuning")
     ap.add_argument("--sections", default="uniform,reductions,uneven,serve",
                     help="extra polymul sections to run (comma list of uniform, reductions, uneven, serve; "
                          "empty for none)")
@@ -357,8 +359,9 @@ def run_gpu(args, ws, rank, local):
         if "reductions" in secs:
             extra["polymul_alg2_vs_alg3_4096x2048"] = bp.reduction_ab(m, torch)
         if "uneven" in secs:
+            cfg = tuple(int(x) for x in args.batch_config.split(",")) if args.batch_config else None
             extra["polymul_uneven_10000"] = bp.uneven_batch(m, torch, peaks, cpu=not args.no_cpu_baseline,
-                                                            per_product=not args.no_per_product)
+                                                            per_product=not args.no_per_product, config=cfg)
         if "serve" in secs:
             extra["serve_50000"] = bp.serve_stream(m, torch)
         if secs:

@@ -150,7 +150,7 @@ def reduction_ab(m, torch, steps=20, warmup=3):
     return res
 
 
-def uneven_batch(m, torch, peaks, steps=10, warmup=3, cpu=True, per_product=True):
+def uneven_batch(m, torch, peaks, steps=10, warmup=3, cpu=True, per_product=True, config=None):
     import oracle
     wl = synth.batch_uneven()
     da = torch.from_numpy(wl.a.view(np.int32)).cuda()
@@ -158,7 +158,11 @@ def uneven_batch(m, torch, peaks, steps=10, warmup=3, cpu=True, per_product=True
     dc = torch.empty(wl.c_size, dtype=torch.int32, device="cuda")
     plan = m.PolymulBatchPlan.from_packed(wl.primes, da, wl.a_off, wl.la, db, wl.b_off, wl.lb, dc, wl.c_off)
     t0 = time.perf_counter()
-    cfg = plan.tune(trials=2)
+    if config is None:
+        cfg = plan.tune(trials=2)
+    else:                                   # fixed launch shape (ctas_per_sm, order, kernel): no tuning launches
+        plan.config = m.PolymulBatchConfig(*config)
+        cfg = plan.config
     tune_s = time.perf_counter() - t0
     for _ in range(warmup):
         plan.run_graph()
@@ -179,7 +183,8 @@ def uneven_batch(m, torch, peaks, steps=10, warmup=3, cpu=True, per_product=True
                        "{2013265921, 469762049, 754974721}, N padded to powers of two",
            "value": coeffs / ms / 1e6, "unit": "Gcoef/s", "ms": ms, "steps": steps, "warmup": warmup,
            "launch": "one persistent kernel per batch, replayed from a CUDA graph",
-           "tuned_config": {"ctas_per_sm": cfg.ctas_per_sm, "order": cfg.order}, "tune_s": tune_s,
+           "tuned_config": {"ctas_per_sm": cfg.ctas_per_sm, "order": cfg.order, "kernel": cfg.kernel,
+                            "tuned": config is None}, "tune_s": tune_s,
            "workspace_bytes": plan.workspace_bytes(), "l2": "operands + scratch (2.4 GB) larger than L2",
            "gpu_launches": steps,
            "roofline": {"bound": "alu", "kernel": "k_polymul_batch", "achieved": ops / (ms / 1e3) / 1e12,

@@ -83,6 +83,16 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p)
     return v;
 }
 
+// Coherent at GPU scope but without acquire ordering: polling with it does
+// not invalidate the SM's L1 (which an acquire load does, for every CTA on
+// the SM) on each poll.
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 // Thread 0 only: wait until *ctr >= target, bounded by iterations and time.
 // Gives up at once when another CTA has already recorded an expired wait, so
 // a failed batch costs at most about one wait limit in total.
@@ -91,8 +101,11 @@ __device__ bool bounded_wait(const uint32_t *ctr, uint32_t target, const BatchAr
     const uint32_t *err = A.sync + 1;
     const unsigned long long t0 = globaltimer();
     for (uint32_t it = 0;; it++) {
-        if (ld_acquire(ctr) >= target) return true;
-        if (ld_acquire(err) != 0u || it >= A.wait_iters || globaltimer() - t0 > A.wait_ns) return false;
+        // Relaxed polls; once the count is reached, one acquire load (the
+        // counter only grows, so it sees it too) orders the caller's reads of
+        // the producers' data after their writes.
+        if (ld_relaxed(ctr) >= target) return ld_acquire(ctr) >= target;
+        if (ld_relaxed(err) != 0u || it >= A.wait_iters || globaltimer() - t0 > A.wait_ns) return false;
         __nanosleep(200);
     }
 }
