@@ -51,7 +51,7 @@ template <int LOGN>
 __global__ void __launch_bounds__(teams_of<LOGN>() * nt_of<LOGN>())
 k_ntt_fwd(NttArgs A)
 {
-    constexpr int N = 1 << LOGN, NT = nt_of<LOGN>(), NP = Sched<LOGN>::kPasses;
+    constexpr int N = 1 << LOGN, NT = nt_of<LOGN>(), NP = SchedFor<LOGN, NT>::kPasses;
     extern __shared__ __align__(16) uint32_t smem[];
     const int team = threadIdx.x / NT, tid = threadIdx.x - team * NT;
     const size_t prod = static_cast<size_t>(blockIdx.x) * teams_of<LOGN>() + team;
@@ -71,7 +71,7 @@ template <int LOGN>
 __global__ void __launch_bounds__(teams_of<LOGN>() * nt_of<LOGN>())
 k_ntt_inv(NttArgs A)
 {
-    constexpr int N = 1 << LOGN, NT = nt_of<LOGN>(), NP = Sched<LOGN>::kPasses;
+    constexpr int N = 1 << LOGN, NT = nt_of<LOGN>(), NP = SchedFor<LOGN, NT>::kPasses;
     extern __shared__ __align__(16) uint32_t smem[];
     const int team = threadIdx.x / NT, tid = threadIdx.x - team * NT;
     const size_t prod = static_cast<size_t>(blockIdx.x) * teams_of<LOGN>() + team;

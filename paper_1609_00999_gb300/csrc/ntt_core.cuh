@@ -208,21 +208,30 @@ __device__ __forceinline__ void gs_group(uint32_t (&x)[NARR][1 << E], const uint
     }
 }
 
-// Pass schedule for a sub-transform of 2^LOGN elements: ceil(LOGN / 4)
-// passes of (nearly) equal numbers of levels, at most 4 each.
-template <int LOGN>
+// Pass schedule for a sub-transform of 2^LOGN elements: ceil(LOGN / EMAX)
+// passes of (nearly) equal numbers of levels, at most EMAX each, larger
+// passes first.
+template <int LOGN, int EMAX = 4>
 struct Sched {
-    static constexpr int kPasses = LOGN <= 0 ? 0 : (LOGN + 3) / 4;
+    static constexpr int kPasses = LOGN <= 0 ? 0 : (LOGN + EMAX - 1) / EMAX;
     static constexpr int levels(int i) { return LOGN / kPasses + (i < LOGN % kPasses ? 1 : 0); }
     static constexpr int start(int i) { return i == 0 ? 0 : start(i - 1) + levels(i - 1); }
 };
+
+constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x / 2); }
+
+// Schedule for NT threads: a pass covers up to 4 levels (radix-16 groups),
+// 5 (radix-32) when each thread holds 32 or more elements per array, which
+// saves a shared-memory round trip for 2^13 elements on 256 threads.
+template <int LOGN, int NT>
+using SchedFor = Sched<LOGN, (LOGN - ilog2(NT) >= 5 ? 5 : 4)>;
 
 // Geometry of pass I of a 2^LOGN sub-transform processed by NT threads, each
 // holding EPT = 2^LOGN / NT elements per array (EPT / 2^E groups).
 template <int LOGN, int NT, int I>
 struct PassGeom {
-    static constexpr int S0 = Sched<LOGN>::start(I);
-    static constexpr int E = Sched<LOGN>::levels(I);
+    static constexpr int S0 = SchedFor<LOGN, NT>::start(I);
+    static constexpr int E = SchedFor<LOGN, NT>::levels(I);
     static constexpr int G = 1 << E;
     static constexpr int LOG_HMIN = LOGN - S0 - E;
     static constexpr int HMIN = 1 << LOG_HMIN;
@@ -361,7 +370,7 @@ template <int LOGN, int NT, bool BASE0, class RED = RedAlg2, class L>
 __device__ __forceinline__ void fused_middle_pass(const L (&lay)[2], int tid, const uint32_t *__restrict__ tw,
                                                   const uint32_t *__restrict__ itw, int s_base, int b, Mod m)
 {
-    using PL = PassGeom<LOGN, NT, Sched<LOGN>::kPasses - 1>;
+    using PL = PassGeom<LOGN, NT, SchedFor<LOGN, NT>::kPasses - 1>;
 #pragma unroll
     for (int r = 0; r < PL::GPT; r++) {
         const int base = PL::base(tid, r), blk = (b << PL::S0) + PL::blk(tid, r);

@@ -89,7 +89,7 @@ __device__ __forceinline__ void polymul_team(uint32_t *sm, int tid, const uint32
                                              const uint32_t *__restrict__ tw, const uint32_t *__restrict__ itw, int s_base,
                                              int b_idx, uint32_t p, uint32_t pp, uint32_t k_scale)
 {
-    constexpr int N = 1 << LOGN, NP = Sched<LOGN>::kPasses;
+    constexpr int N = 1 << LOGN, NP = SchedFor<LOGN, NT>::kPasses;
     const Mod md{p, pp};
     if constexpr (LOGN == 0) {
         if (lc > 0) {

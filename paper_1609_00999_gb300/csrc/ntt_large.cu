@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(ColCfg<K1>::THREADS)
 k_col(ColArgs A, size_t prod0)
 {
     using CF = ColCfg<K1>;
-    constexpr int NP = Sched<K1>::kPasses;
+    constexpr int NP = SchedFor<K1, ColCfg<K1>::NT1>::kPasses;
     extern __shared__ __align__(16) uint32_t smem[];
     const bool op1 = blockIdx.y != 0;   // operand select without indexing the parameter arrays
     const size_t prod = prod0 + blockIdx.z;
@@ -126,7 +126,7 @@ template <int K2, bool INVERSE>
 __global__ void __launch_bounds__(nt_of<K2>())
 k_row_ntt(RowNttArgs A, size_t prod0)
 {
-    constexpr int N2 = 1 << K2, NT = nt_of<K2>(), NP = Sched<K2>::kPasses;
+    constexpr int N2 = 1 << K2, NT = nt_of<K2>(), NP = SchedFor<K2, NT>::kPasses;
     extern __shared__ __align__(16) uint32_t smem[];
     const size_t prod = prod0 + blockIdx.y;
     const int r = blockIdx.x;

@@ -153,7 +153,7 @@ __device__ __forceinline__ void col_tile(uint32_t *smem, const Prod &P, const Pr
 {
     using CF = ColTile<K1>;
     using TS = TileShare<CF>;
-    constexpr int NP = Sched<K1>::kPasses;
+    constexpr int NP = SchedFor<K1, ColTile<K1>::NT1>::kPasses;
     constexpr int NARR = INV ? 1 : 2;
     const size_t n = size_t{1} << P.k;
     const size_t o0 = static_cast<size_t>(tile) * CF::C;
