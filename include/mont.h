@@ -268,10 +268,10 @@ int polymul_batch_plan_tune(polymul_batch_plan *plan, cudaStream_t stream, int t
 /* Bound of every device-side wait of the plan (default 2^22 polls, 2 s). */
 int polymul_batch_plan_set_wait_limit(polymul_batch_plan *plan, uint32_t iterations, uint64_t nanoseconds);
 
-/* Failure-detection test hook: makes the first split product wait for a
- * column tile that does not exist, so its bounded waits expire and
+/* Failure-detection test hook: makes the first product with N > 2^15 wait
+ * for a column tile that does not exist, so its bounded waits expire and
  * polymul_batch_status reports MONT_ETIMEOUT.  MONT_EINVAL if the batch has
- * no product with N > 2^13. */
+ * no product with N > 2^15 (smaller ones run without cross-CTA waits). */
 int polymul_batch_plan_inject_stall(polymul_batch_plan *plan);
 
 /* ------------------------------------------------------------------------

@@ -13,9 +13,10 @@ constexpr int kSmallLog = 13;      // N <= 2^13: whole product in one CTA
 constexpr int kRowLog = 13;        // row size 2^13 for split products (N > 2^13)
 constexpr int kMaxColLog = 8;      // K1 <= 8: N <= 2^21 in a batch
 constexpr int kMaxRegColLog = 4;   // K1 <= 4: column levels in registers
+constexpr int kWholeMaxLog = 15;   // split products up to 2^15: one CTA runs all their jobs
 constexpr int kMaxPrimes = 8;
 
-enum : uint32_t { JOB_SMALL = 0, JOB_COLF = 1, JOB_ROW = 2, JOB_COLI = 3 };
+enum : uint32_t { JOB_SMALL = 0, JOB_COLF = 1, JOB_ROW = 2, JOB_COLI = 3, JOB_WHOLE = 4 };
 
 struct Job {
     uint32_t type, k, prod, idx;   // idx: tile / row index, or the number of products of a SMALL job

@@ -74,6 +74,15 @@ int ensure_smem(K kernel, size_t bytes)
                : MONT_ECUDA;
 }
 
+// Operand loads of a product: the read-only path for a product's own inputs,
+// a coherent load for rows of scratch written earlier in the same kernel.
+template <bool READ_ONLY>
+__device__ __forceinline__ uint32_t load_operand(const uint32_t *p)
+{
+    if constexpr (READ_ONLY) return __ldg(p);
+    else return *p;
+}
+
 // One product (or one row block of a product) by one team of NT threads
 // (nt_of<LOGN>() by default, fewer when each thread takes several groups per
 // pass) with team_smem_words<LOGN>() words of shared memory at sm:
@@ -108,8 +117,8 @@ __device__ __forceinline__ void polymul_team(uint32_t *sm, int tid, const uint32
 #pragma unroll
                 for (int t = 0; t < P0::G; t++) {
                     const int j = base + t * P0::HMIN;
-                    x[0][t] = j < la32 ? __ldg(ga + j) : 0u;
-                    const uint32_t bj = j < lb32 ? __ldg(gb + j) : 0u;
+                    x[0][t] = j < la32 ? load_operand<BASE0>(ga + j) : 0u;
+                    const uint32_t bj = j < lb32 ? load_operand<BASE0>(gb + j) : 0u;
                     x[1][t] = SCALE_B ? RED::mul(bj, k_scale, md) : bj;
                 }
                 ct_group<P0::E, 2, BASE0, RED>(x, tw, s_base, b_idx, md);
@@ -135,7 +144,7 @@ __device__ __forceinline__ void polymul_team(uint32_t *sm, int tid, const uint32
 #pragma unroll
                     for (int t = 0; t < P0::G; t++) {
                         const int j = base + t * P0::HMIN;
-                        const uint32_t v = j < len ? __ldg(g + j) : 0u;
+                        const uint32_t v = j < len ? load_operand<BASE0>(g + j) : 0u;
                         x[0][t] = (SCALE_B && a) ? RED::mul(v, k_scale, md) : v;
                     }
                     ct_group<P0::E, 1, BASE0, RED>(x, tw, s_base, b_idx, md);

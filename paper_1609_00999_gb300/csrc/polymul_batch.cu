@@ -10,8 +10,10 @@
 // (forward row levels, pointwise product, inverse row levels), COLI jobs run
 // the inverse column levels of a block of columns and write c.  Columns of
 // up to 2^4 elements are transformed in registers straight from and to
-// global memory; longer ones go through shared-memory tiles.  Scratch: 2N
-// words per large product.
+// global memory; longer ones go through shared-memory tiles.  Split products
+// up to 2^15 run as one WHOLE job instead: one CTA does their column, row
+// and output jobs in sequence (no waits; their scratch stays in L2).
+// Scratch: 2N words per large product.
 //
 // CTAs of the persistent grid claim jobs in list order with one atomic
 // counter (each CTA one job ahead of the one it runs).  A ROW job waits until every COLF tile of its product has
@@ -274,6 +276,36 @@ __device__ __forceinline__ void col_regs(const Prod &P, const PrimeInfo &pr, uin
     }
 }
 
+// All jobs of one split product by this CTA, in dependency order; the
+// barriers make each phase's scratch writes visible to the next phase's
+// (coherent) loads.
+template <int K1>
+__device__ __forceinline__ void whole_job(uint32_t *smem, const Prod &P, const PrimeInfo &pr)
+{
+    static_assert(K1 <= kMaxRegColLog, "whole jobs use register column passes");
+    const size_t n = size_t{1} << P.k;
+    for (uint32_t t = 0; t < P.ntiles; t++) col_regs<K1, false>(P, pr, t);
+    __syncthreads();
+    for (uint32_t r = 0; r < P.nrows; r++) {
+        uint32_t *row = P.ws + (static_cast<size_t>(r) << kRowLog);
+        polymul_team<kRowLog, false, false, kThreads>(smem, threadIdx.x, row, size_t{1} << kRowLog, row + n,
+                                                      size_t{1} << kRowLog, row, size_t{1} << kRowLog, pr.tw,
+                                                      pr.itw, K1, static_cast<int>(r), pr.p, pr.pp, 0u);
+        __syncthreads();
+    }
+    for (uint32_t t = 0; t < P.ntiles; t++) col_regs<K1, true>(P, pr, t);
+}
+
+__device__ __forceinline__ void whole_dispatch(uint32_t *smem, const Prod &P, const PrimeInfo &pr)
+{
+    static_assert(kWholeMaxLog - kRowLog <= 2, "extend the dispatch");
+    switch (P.k - kRowLog) {
+    case 1: whole_job<1>(smem, P, pr); break;
+    case 2: whole_job<2>(smem, P, pr); break;
+    default: break;
+    }
+}
+
 template <bool INV>
 __device__ __forceinline__ void col_job(uint32_t *smem, const Prod &P, const PrimeInfo &pr, uint32_t tile)
 {
@@ -351,6 +383,9 @@ __global__ void __launch_bounds__(kThreads, MINB) k_polymul_batch(BatchArgs A)
         const Job J = A.jobs[jid];
         if (J.type == JOB_SMALL) {
             small_dispatch(smem, A, J);
+        } else if (J.type == JOB_WHOLE) {
+            const Prod &P = A.prods[J.prod];
+            whole_dispatch(smem, P, A.primes[P.prime]);
         } else {
             const Prod &P = A.prods[J.prod];
             const PrimeInfo &pr = A.primes[P.prime];
@@ -471,10 +506,16 @@ int batch_build(const polymul_desc *descs, size_t count, BatchHost &out, std::ve
     for (size_t i : small) out.prods.push_back(prods[i]);
     for (size_t i : large) out.prods.push_back(prods[i]);
     const size_t nsmall = small.size();
-    std::vector<Job> colf, sm, row, coli;
+    std::vector<Job> colf, sm, row, coli, whole;
+    std::vector<size_t> piped;   // split products run as column / row / column jobs
     for (size_t i = nsmall; i < count; i++) {
         const Prod &P = out.prods[i];
         const uint32_t id = static_cast<uint32_t>(i);
+        if (P.k <= static_cast<uint32_t>(kWholeMaxLog)) {
+            whole.push_back(Job{JOB_WHOLE, P.k, id, 0});
+            continue;
+        }
+        piped.push_back(i);
         for (uint32_t t = 0; t < P.ntiles; t++) colf.push_back(Job{JOB_COLF, P.k, id, t});
         for (uint32_t r = 0; r < P.nrows; r++) row.push_back(Job{JOB_ROW, P.k, id, r});
         for (uint32_t t = 0; t < P.ntiles; t++) coli.push_back(Job{JOB_COLI, P.k, id, t});
@@ -487,27 +528,32 @@ int batch_build(const polymul_desc *descs, size_t count, BatchHost &out, std::ve
         sm.push_back(Job{JOB_SMALL, k, static_cast<uint32_t>(s), static_cast<uint32_t>(e - s)});
         s = e;
     }
-    // order 0: split products' column tiles first, whole small products fill
-    // the time until their rows can start; order 1: small products first.
+    // Whole jobs are the longest: largest first.
+    std::stable_sort(whole.begin(), whole.end(), [](const Job &x, const Job &y) { return x.k > y.k; });
+    // order 0: split products' column tiles first, whole and small products
+    // fill the time until their rows can start; order 1: whole and small
+    // products first.
     for (int order = 0; order < 2; order++) {
         std::vector<Job> &jobs = out.jobs[order];
-        const std::vector<Job> *seq0[4] = {&colf, &sm, &row, &coli};
-        const std::vector<Job> *seq1[4] = {&sm, &colf, &row, &coli};
+        const std::vector<Job> *seq0[5] = {&colf, &whole, &sm, &row, &coli};
+        const std::vector<Job> *seq1[5] = {&whole, &sm, &colf, &row, &coli};
         for (const std::vector<Job> *v : (order == 0 ? seq0 : seq1)) jobs.insert(jobs.end(), v->begin(), v->end());
     }
-    // orders 2, 3: rounds r = 0, 1, ...: column tiles of split product r, rows
-    // of product r - D, output tiles of product r - 2D, and an even share of
-    // the small products.  Every job waits only on jobs of earlier rounds.
-    const size_t nlarge = count - nsmall;
+    // orders 2, 3: the whole jobs, then rounds r = 0, 1, ...: column tiles of
+    // pipelined product r, rows of product r - D, output tiles of product
+    // r - 2D, and an even share of the small products.  Every job waits only
+    // on jobs of earlier rounds.
+    const size_t nlarge = piped.size();
     std::vector<size_t> colf_at(nlarge + 1, 0), row_at(nlarge + 1, 0);
     for (size_t i = 0; i < nlarge; i++) {
-        colf_at[i + 1] = colf_at[i] + out.prods[nsmall + i].ntiles;
-        row_at[i + 1] = row_at[i] + out.prods[nsmall + i].nrows;
+        colf_at[i + 1] = colf_at[i] + out.prods[piped[i]].ntiles;
+        row_at[i + 1] = row_at[i] + out.prods[piped[i]].nrows;
     }
     for (int order = 2; order < kJobOrders; order++) {
         const size_t D = order == 2 ? 32 : 64;
         std::vector<Job> &jobs = out.jobs[order];
-        jobs.reserve(colf.size() + sm.size() + row.size() + coli.size());
+        jobs.reserve(whole.size() + colf.size() + sm.size() + row.size() + coli.size());
+        jobs.insert(jobs.end(), whole.begin(), whole.end());
         const size_t rounds = nlarge + 2 * D;
         size_t si = 0;
         for (size_t r = 0; r < rounds; r++) {
@@ -813,16 +859,17 @@ extern "C" int polymul_batch_plan_tune(polymul_batch_plan *plan, cudaStream_t st
     return polymul_batch_status(plan, stream);
 }
 
-// Test hook for failure detection: makes the first split product expect one
-// more column tile than exists, so its row jobs wait on a count that is
-// never reached; the bounded waits expire and the batch reports
-// MONT_ETIMEOUT.  Undone by recreating the plan.
+// Test hook for failure detection: makes the first product that runs as
+// column / row / column jobs (N > 2^15) expect one more column tile than
+// exists, so its row jobs wait on a count that is never reached; the bounded
+// waits expire and the batch reports MONT_ETIMEOUT.  Undone by recreating
+// the plan.
 extern "C" int polymul_batch_plan_inject_stall(polymul_batch_plan *plan)
 {
     if (!plan) return MONT_EINVAL;
     for (size_t i = 0; i < plan->host.prods.size(); i++) {
         mont::Prod &P = plan->host.prods[i];
-        if (P.k <= static_cast<uint32_t>(mont::kSmallLog)) continue;
+        if (P.k <= static_cast<uint32_t>(mont::kWholeMaxLog)) continue;   // no cross-CTA waits
         P.ntiles += 1;
         if (cudaMemcpy(plan->d_prods + i, &P, sizeof(mont::Prod), cudaMemcpyHostToDevice) != cudaSuccess)
             return MONT_ECUDA;

@@ -102,7 +102,7 @@ def test_uneven_config_sample(m):
 
 def test_bounded_wait_reports_timeout_and_context_survives(m):
     import torch
-    wl = synth.UnevenBatch([synth.P1, synth.P2], [5000, 10], [5000, 10], (603,))
+    wl = synth.UnevenBatch([synth.P1, synth.P2], [20000, 10], [20000, 10], (603,))   # N = 2^16: cross-CTA waits
     da, db = to_dev(wl.a), to_dev(wl.b)
     dc = torch.zeros(wl.c_size, dtype=torch.int32, device="cuda")
     plan = m.PolymulBatchPlan.from_packed(wl.primes, da, wl.a_off, wl.la, db, wl.b_off, wl.lb, dc, wl.c_off)
