@@ -83,32 +83,47 @@ __device__ __forceinline__ uint32_t load_operand(const uint32_t *p)
     else return *p;
 }
 
+// Operand source of a product: element j (< 2^LOGN) of operand 0 (a) or 1
+// (b), zero at and beyond the operand's length, b multiplied by k_scale
+// through the reduction (b N^-1 R^2 R^-1 = b N^-1 R).
+template <bool READ_ONLY, bool SCALE_B, class RED>
+struct PlainLoad {
+    const uint32_t *a, *b;
+    int la, lb;
+    uint32_t k_scale;
+    Mod m;
+    __device__ __forceinline__ uint32_t operator()(int arr, int j) const
+    {
+        const uint32_t *g = arr ? b : a;
+        const uint32_t v = j < (arr ? lb : la) ? load_operand<READ_ONLY>(g + j) : 0u;
+        return (SCALE_B && arr) ? RED::mul(v, k_scale, m) : v;
+    }
+};
+
 // One product (or one row block of a product) by one team of NT threads
 // (nt_of<LOGN>() by default, fewer when each thread takes several groups per
 // pass) with team_smem_words<LOGN>() words of shared memory at sm:
-// c[0 .. lc) = inverse( forward(a) * forward(b * scale) ), where the
-// sub-transform is block b_idx of the levels s_base .. s_base + LOGN - 1 of
-// the whole transform (s_base = 0, b_idx = 0 for a complete product).
-// Reads of a and b (lengths la, lb, zero beyond) all happen before the first
-// barrier, so gc may alias ga (in-place row passes).  Every thread of the CTA
-// must call it (it contains __syncthreads).  la, lb, lc <= 2^LOGN.
-template <int LOGN, bool BASE0, bool SCALE_B, int NT = nt_of<LOGN>(), class RED = RedAlg2>
-__device__ __forceinline__ void polymul_team(uint32_t *sm, int tid, const uint32_t *ga, size_t la,
-                                             const uint32_t *gb, size_t lb, uint32_t *gc, size_t lc,
-                                             const uint32_t *__restrict__ tw, const uint32_t *__restrict__ itw, int s_base,
-                                             int b_idx, uint32_t p, uint32_t pp, uint32_t k_scale)
+// c[0 .. lc) = inverse( forward(A) * forward(B) ), A and B element j being
+// ld(0, j) and ld(1, j), where the sub-transform is block b_idx of the
+// levels s_base .. s_base + LOGN - 1 of the whole transform (s_base = 0,
+// b_idx = 0 for a complete product; BASE0 then also means ld returns reduced
+// values, otherwise values below 2P are allowed).  All operand reads happen
+// before the first barrier, so gc may alias the operands (in-place row
+// passes).  Every thread of the CTA must call it (it contains
+// __syncthreads).  lc <= 2^LOGN.
+template <int LOGN, bool BASE0, int NT, class RED, class LD>
+__device__ __forceinline__ void polymul_team_ld(uint32_t *sm, int tid, const LD &ld, uint32_t *gc, size_t lc,
+                                                const uint32_t *__restrict__ tw, const uint32_t *__restrict__ itw,
+                                                int s_base, int b_idx, Mod md)
 {
     constexpr int N = 1 << LOGN, NP = SchedFor<LOGN, NT>::kPasses;
-    const Mod md{p, pp};
+    const uint32_t p = md.p;
     if constexpr (LOGN == 0) {
-        if (lc > 0) {
-            const uint32_t bb = SCALE_B ? RED::mul(gb[0], k_scale, md) : gb[0];
-            gc[0] = RED::mul(ga[0], bb, md);
-        }
+        if (lc > 0) gc[0] = RED::mul(ld(0, 0), ld(1, 0), md);
     } else {
         const PadLayout lay[2] = {{sm}, {sm + PadLayout::words(N)}};
         using P0 = PassGeom<LOGN, NT, 0>;
-        const int la32 = static_cast<int>(la), lb32 = static_cast<int>(lb), lc32 = static_cast<int>(lc);
+        const int lc32 = static_cast<int>(lc);
         if constexpr (NP == 1) {
 #pragma unroll
             for (int r = 0; r < P0::GPT; r++) {
@@ -117,9 +132,8 @@ __device__ __forceinline__ void polymul_team(uint32_t *sm, int tid, const uint32
 #pragma unroll
                 for (int t = 0; t < P0::G; t++) {
                     const int j = base + t * P0::HMIN;
-                    x[0][t] = j < la32 ? load_operand<BASE0>(ga + j) : 0u;
-                    const uint32_t bj = j < lb32 ? load_operand<BASE0>(gb + j) : 0u;
-                    x[1][t] = SCALE_B ? RED::mul(bj, k_scale, md) : bj;
+                    x[0][t] = ld(0, j);
+                    x[1][t] = ld(1, j);
                 }
                 ct_group<P0::E, 2, BASE0, RED>(x, tw, s_base, b_idx, md);
                 uint32_t y[1][P0::G];
@@ -135,18 +149,12 @@ __device__ __forceinline__ void polymul_team(uint32_t *sm, int tid, const uint32
         } else {
 #pragma unroll
             for (int a = 0; a < 2; a++) {
-                const uint32_t *g = a ? gb : ga;
-                const int len = a ? lb32 : la32;
 #pragma unroll
                 for (int r = 0; r < P0::GPT; r++) {
                     const int base = P0::base(tid, r);
                     uint32_t x[1][P0::G];
 #pragma unroll
-                    for (int t = 0; t < P0::G; t++) {
-                        const int j = base + t * P0::HMIN;
-                        const uint32_t v = j < len ? load_operand<BASE0>(g + j) : 0u;
-                        x[0][t] = (SCALE_B && a) ? RED::mul(v, k_scale, md) : v;
-                    }
+                    for (int t = 0; t < P0::G; t++) x[0][t] = ld(a, base + t * P0::HMIN);
                     ct_group<P0::E, 1, BASE0, RED>(x, tw, s_base, b_idx, md);
 #pragma unroll
                     for (int t = 0; t < P0::G; t++) elem(lay[a], base, t * P0::HMIN) = x[0][t];
@@ -174,6 +182,20 @@ __device__ __forceinline__ void polymul_team(uint32_t *sm, int tid, const uint32
             }
         }
     }
+}
+
+// polymul_team_ld on operand arrays a (length la) and b (length lb): the
+// product's own inputs (read-only path) when BASE0, scratch rows (coherent
+// loads) otherwise; b multiplied by k_scale on load when SCALE_B.
+template <int LOGN, bool BASE0, bool SCALE_B, int NT = nt_of<LOGN>(), class RED = RedAlg2>
+__device__ __forceinline__ void polymul_team(uint32_t *sm, int tid, const uint32_t *ga, size_t la,
+                                             const uint32_t *gb, size_t lb, uint32_t *gc, size_t lc,
+                                             const uint32_t *__restrict__ tw, const uint32_t *__restrict__ itw, int s_base,
+                                             int b_idx, uint32_t p, uint32_t pp, uint32_t k_scale)
+{
+    const Mod md{p, pp};
+    const PlainLoad<BASE0, SCALE_B, RED> ld{ga, gb, static_cast<int>(la), static_cast<int>(lb), k_scale, md};
+    polymul_team_ld<LOGN, BASE0, NT, RED>(sm, tid, ld, gc, lc, tw, itw, s_base, b_idx, md);
 }
 
 namespace {

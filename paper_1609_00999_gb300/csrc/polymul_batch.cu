@@ -11,8 +11,9 @@
 // the inverse column levels of a block of columns and write c.  Columns of
 // up to 2^4 elements are transformed in registers straight from and to
 // global memory; longer ones go through shared-memory tiles.  Split products
-// up to 2^15 run as one WHOLE job instead: one CTA does their column, row
-// and output jobs in sequence (no waits; their scratch stays in L2).
+// up to 2^15 run as one WHOLE job instead: one CTA runs their rows (column
+// levels computed on load) and the output column pass in sequence (no
+// waits; their scratch stays in L2).
 // Scratch: 2N words per large product.
 //
 // CTAs of the persistent grid claim jobs in list order with one atomic
@@ -276,21 +277,70 @@ __device__ __forceinline__ void col_regs(const Prod &P, const PrimeInfo &pr, uin
     }
 }
 
-// All jobs of one split product by this CTA, in dependency order; the
-// barriers make each phase's scratch writes visible to the next phase's
-// (coherent) loads.
+// Row r of a split product with K1 <= 2 column levels, the column levels
+// computed as the row is loaded: element j of the row is element r of the
+// forward column transform of the 2^K1 inputs at j + i 2^13 (levels
+// 0 .. K1-1, block 0 of the transform: twiddles tw[1 .. 2^K1 - 1]); b's is
+// then multiplied by k_scale (the transform is linear, so this equals
+// scaling its inputs).  Inputs reduced, results below 2P (lazy forward
+// values, as the row passes take them).
+template <int K1>
+struct ColFusedLoad {
+    const uint32_t *a, *b;
+    uint32_t la, lb, k_scale;
+    Mod m;
+    const uint32_t *tw;
+    int r;
+    __device__ __forceinline__ uint32_t operator()(int arr, int j) const
+    {
+        const uint32_t *g = arr ? b : a;
+        const uint32_t len = arr ? lb : la;
+        uint32_t x[1][1 << K1];
+#pragma unroll
+        for (int i = 0; i < (1 << K1); i++) {
+            const uint32_t idx = static_cast<uint32_t>(j) + (static_cast<uint32_t>(i) << kRowLog);
+            x[0][i] = idx < len ? __ldg(g + idx) : 0u;
+        }
+        ct_group<K1, 1, true>(x, tw, 0, 0, m);
+        uint32_t v = x[0][0];
+#pragma unroll
+        for (int i = 1; i < (1 << K1); i++) v = r == i ? x[0][i] : v;
+        return arr ? RedAlg2::mul(v, k_scale, m) : v;
+    }
+};
+
+// Operand source reading a row already staged in shared memory (padded
+// layout); pass 0 then transforms it in place.
+struct StagedLoad {
+    PadLayout lay[2];
+    __device__ __forceinline__ uint32_t operator()(int arr, int j) const { return lay[arr][j]; }
+};
+
+// All jobs of one split product (K1 <= 2) by this CTA: each row stages its
+// operands into shared memory with the column levels computed as they are
+// loaded (no forward scratch round trip; the inputs are read 2^K1 times,
+// from L2 after the first), runs the row levels, the pointwise product and
+// the inverse row levels into scratch; then the inverse column pass writes
+// c.  The barriers make the rows' scratch writes visible to the column
+// pass's coherent loads.
 template <int K1>
 __device__ __forceinline__ void whole_job(uint32_t *smem, const Prod &P, const PrimeInfo &pr)
 {
-    static_assert(K1 <= kMaxRegColLog, "whole jobs use register column passes");
-    const size_t n = size_t{1} << P.k;
-    for (uint32_t t = 0; t < P.ntiles; t++) col_regs<K1, false>(P, pr, t);
-    __syncthreads();
+    static_assert(K1 <= 2, "whole jobs recompute at most two column levels per row");
+    constexpr int N2 = 1 << kRowLog;
+    const Mod md{pr.p, pr.pp};
+    const StagedLoad staged{{{smem}, {smem + PadLayout::words(N2)}}};
     for (uint32_t r = 0; r < P.nrows; r++) {
+        const ColFusedLoad<K1> ld{P.a, P.b, P.la, P.lb, P.k_scale, md, pr.tw, static_cast<int>(r)};
+#pragma unroll 2
+        for (int j = threadIdx.x; j < N2; j += kThreads) {
+            staged.lay[0][j] = ld(0, j);
+            staged.lay[1][j] = ld(1, j);
+        }
+        __syncthreads();
         uint32_t *row = P.ws + (static_cast<size_t>(r) << kRowLog);
-        polymul_team<kRowLog, false, false, kThreads>(smem, threadIdx.x, row, size_t{1} << kRowLog, row + n,
-                                                      size_t{1} << kRowLog, row, size_t{1} << kRowLog, pr.tw,
-                                                      pr.itw, K1, static_cast<int>(r), pr.p, pr.pp, 0u);
+        polymul_team_ld<kRowLog, false, kThreads, RedAlg2>(smem, threadIdx.x, staged, row, size_t{1} << kRowLog,
+                                                           pr.tw, pr.itw, K1, static_cast<int>(r), md);
         __syncthreads();
     }
     for (uint32_t t = 0; t < P.ntiles; t++) col_regs<K1, true>(P, pr, t);
