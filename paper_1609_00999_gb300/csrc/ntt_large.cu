@@ -1,16 +1,18 @@
 // ntt_large.cu -- transforms and products with N = 2^K > 2^14 (up to 2^24).
 //
-// The K levels split into K1 column levels and K2 = max(12, K - 10) row
-// levels.  Viewing the N elements as a [2^K1][2^K2] row-major matrix, levels
-// 0 .. K1-1 pair elements of the same column (stride 2^K2) and their
-// twiddles depend only on the row index, so every column is an independent
-// 2^K1-point transform with the table entries 1 .. 2^K1 - 1.  Levels
-// K1 .. K-1 stay inside one row; row r is block r of level K1, so its
-// twiddle for local level l and local block i is entry 2^(K1+l) + (r << l) + i.
+// The K levels split into K1 column levels and K2 row levels (K2 = 12 up
+// to K = 16, K - 4 for K = 17, 18, then max(12, K - 10)).  Viewing the N elements as a
+// [2^K1][2^K2] row-major matrix, levels 0 .. K1-1 pair elements of the same
+// column (stride 2^K2) and their twiddles depend only on the row index, so
+// every column is an independent 2^K1-point transform with the table
+// entries 1 .. 2^K1 - 1.  Levels K1 .. K-1 stay inside one row; row r is
+// block r of level K1, so its twiddle for local level l and local block i
+// is entry 2^(K1+l) + (r << l) + i.
 //
-// Column kernel: a CTA loads a tile of C consecutive columns with coalesced
-// row segments, runs the column levels per column (one team of threads per
-// column), and writes the tile back.  Row kernel: one CTA per row, the same
+// Column kernels: up to four levels in registers, straight from and to
+// global memory (k_col_regs); more levels through a shared-memory tile of C
+// consecutive columns loaded with coalesced row segments, one team of
+// threads per column (k_col).  Row kernel: one CTA per row, the same
 // register passes as the single-CTA kernels.  Forward values between the
 // column and row kernels are lazy ([0, 2P), as inside the passes); the row
 // kernels take them as such and reduce what they finally store.
@@ -71,25 +73,82 @@ k_col(ColArgs A, size_t prod0)
     const uint32_t p = A.p, pp = A.pp;
     auto col = [&](int c) { return ColLayout<CF::SW>{smem + c * CF::STRIDE, (c * CF::MUL) & 31}; };
 
-    for (int i = threadIdx.x; i < CF::C * CF::N1; i += CF::THREADS) {
-        const int t = i / CF::C, c = i % CF::C;
-        const size_t j = o0 + c + (static_cast<size_t>(t) << A.k2);
-        uint32_t v = j < slen ? __ldg(src + j) : 0u;
-        if (scale) v = mont_mul(v, scale, p, pp);
-        col(c)[t] = v;
+    // Tile sweep in row-major order, THREADS elements per step: this thread
+    // always lands on column cT and rows t0 + u S (S = THREADS / C rows per
+    // step), so its elements sit at fixed strides from one base, in global
+    // memory and in its column of shared memory.
+    static_assert(CF::THREADS % CF::C == 0, "tile sweep");
+    constexpr int S = CF::THREADS / CF::C, PER = CF::N1 / S;
+    const int cT = threadIdx.x % CF::C, t0 = threadIdx.x / CF::C;
+    const ColLayout<CF::SW> mine = col(cT);
+    const size_t first = o0 + cT + (static_cast<size_t>(t0) << A.k2), step = static_cast<size_t>(S) << A.k2;
+    const long long room_in = static_cast<long long>(slen) - static_cast<long long>(first);
+    {
+        uint32_t v[PER];
+#pragma unroll
+        for (int u = 0; u < PER; u++) v[u] = static_cast<long long>(u * step) < room_in ? __ldg(src + first + u * step) : 0u;
+#pragma unroll
+        for (int u = 0; u < PER; u++) mine[t0 + u * S] = scale ? mont_mul(v[u], scale, p, pp) : v[u];
     }
     __syncthreads();
     const int c = threadIdx.x / CF::NT1, tid = threadIdx.x % CF::NT1;
     const ColLayout<CF::SW> lay[1] = {col(c)};
     if constexpr (!INVERSE) fwd_passes<K1, CF::NT1, 1, true, 0, NP - 1>(lay, tid, A.tw, 0, 0, Mod{p, pp});
     else inv_passes<K1, CF::NT1, true, NP - 1, 0>(lay[0], tid, A.tw, 0, 0, Mod{p, pp});
-    for (int i = threadIdx.x; i < CF::C * CF::N1; i += CF::THREADS) {
-        const int t = i / CF::C, cc = i % CF::C;
-        const size_t j = o0 + cc + (static_cast<size_t>(t) << A.k2);
-        uint32_t v = col(cc)[t];
+    const long long room_out = static_cast<long long>(A.dst_len) - static_cast<long long>(first);
+#pragma unroll
+    for (int u = 0; u < PER; u++) {
+        uint32_t v = mine[t0 + u * S];
         if (A.post) v = mont_mul(v, A.post, p, pp);
-        if (j < A.dst_len) dst[j] = v;
+        if (static_cast<long long>(u * step) < room_out) dst[first + u * step] = v;
     }
+}
+
+// Column pass in registers for K1 <= 4: each of 128 threads takes G = 16 /
+// 2^K1 consecutive-by-128 columns of one operand (16 elements), loads them
+// straight from global memory (a warp reads 32 consecutive words of one row
+// per load, all of a thread's loads in flight together), runs the column
+// levels as the G arrays of one register group (they share twiddles:
+// levels 0 .. K1-1, block 0) and stores them back: no shared memory, no
+// barriers.
+constexpr int kRegColThreads = 128;
+
+template <int K1, bool INVERSE>
+__global__ void __launch_bounds__(kRegColThreads) k_col_regs(ColArgs A, size_t prod0)
+{
+    constexpr int N1 = 1 << K1, G = 16 / N1;
+    const bool op1 = blockIdx.y != 0;
+    const size_t prod = prod0 + blockIdx.z;
+    const uint32_t *src = (op1 ? A.src[1] : A.src[0]) + prod * (op1 ? A.src_stride[1] : A.src_stride[0]);
+    const size_t slen = op1 ? A.src_len[1] : A.src_len[0];
+    uint32_t *dst = (op1 ? A.dst[1] : A.dst[0]) + prod * A.dst_stride;
+    const uint32_t scale = op1 ? A.scale[1] : A.scale[0];
+    const uint32_t p = A.p, pp = A.pp;
+    const size_t c0 = static_cast<size_t>(blockIdx.x) * (kRegColThreads * G) + threadIdx.x;
+    uint32_t x[G][N1];
+#pragma unroll
+    for (int g = 0; g < G; g++)
+#pragma unroll
+        for (int t = 0; t < N1; t++) {
+            const size_t j = c0 + g * kRegColThreads + (static_cast<size_t>(t) << A.k2);
+            x[g][t] = j < slen ? __ldg(src + j) : 0u;
+        }
+    if (scale)
+#pragma unroll
+        for (int g = 0; g < G; g++)
+#pragma unroll
+            for (int t = 0; t < N1; t++) x[g][t] = mont_mul(x[g][t], scale, p, pp);
+    if constexpr (!INVERSE) ct_group<K1, G, true>(x, A.tw, 0, 0, Mod{p, pp});
+    else gs_group<K1, G, true>(x, A.tw, 0, 0, Mod{p, pp});
+#pragma unroll
+    for (int g = 0; g < G; g++)
+#pragma unroll
+        for (int t = 0; t < N1; t++) {
+            const size_t j = c0 + g * kRegColThreads + (static_cast<size_t>(t) << A.k2);
+            uint32_t v = x[g][t];
+            if (A.post) v = mont_mul(v, A.post, p, pp);
+            if (j < A.dst_len) dst[j] = v;
+        }
 }
 
 struct RowArgs {
@@ -174,6 +233,20 @@ int launch_col(const ColArgs &A, size_t nops, size_t count, cudaStream_t s)
     return MONT_OK;
 }
 
+template <int K1, bool INVERSE>
+int launch_col_regs(const ColArgs &A, size_t nops, size_t count, cudaStream_t s)
+{
+    constexpr int COLS = kRegColThreads * (16 >> K1);
+    const size_t n2 = size_t{1} << A.k2;
+    for (size_t first = 0; first < count; first += kMaxGridZ) {
+        const unsigned z = static_cast<unsigned>(std::min<size_t>(kMaxGridZ, count - first));
+        dim3 grid(static_cast<unsigned>(n2 / COLS), static_cast<unsigned>(nops), z);
+        k_col_regs<K1, INVERSE><<<grid, kRegColThreads, 0, s>>>(A, first);
+        if (cudaGetLastError() != cudaSuccess) return MONT_ECUDA;
+    }
+    return MONT_OK;
+}
+
 template <int K2>
 int launch_row_polymul(const RowArgs &A, size_t count, cudaStream_t s)
 {
@@ -202,20 +275,30 @@ int launch_row_ntt(const RowNttArgs &A, size_t count, cudaStream_t s)
     return MONT_OK;
 }
 
+// Row levels K2: 2^12 rows up to N = 2^16; rows of 2^13 and 2^14 for
+// N = 2^17 and 2^18, which keeps four column levels (register column
+// passes); beyond, 2^12 rows again (rows of 2^14 run one 1024-thread CTA per
+// SM and lose to more column levels) until K - 10 > 12.
 int split_k2(int k)
 {
+    if (k <= 16) return 12;
+    if (k <= 18) return k - 4;
     return std::max(12, k - 10);
 }
 
-#define MONT_K1_CASES(X) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10)
+#define MONT_K1_TILE_CASES(X) X(5) X(6) X(7) X(8) X(9) X(10)
 
 template <bool INVERSE>
 int dispatch_col(int k1, const ColArgs &A, size_t nops, size_t count, cudaStream_t s)
 {
     switch (k1) {
+    case 1: return launch_col_regs<1, INVERSE>(A, nops, count, s);
+    case 2: return launch_col_regs<2, INVERSE>(A, nops, count, s);
+    case 3: return launch_col_regs<3, INVERSE>(A, nops, count, s);
+    case 4: return launch_col_regs<4, INVERSE>(A, nops, count, s);
 #define X(K) \
     case K: return launch_col<K, INVERSE>(A, nops, count, s);
-        MONT_K1_CASES(X)
+        MONT_K1_TILE_CASES(X)
 #undef X
     default: return MONT_EUNSUPPORTED;
     }
