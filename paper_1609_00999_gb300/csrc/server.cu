@@ -36,7 +36,7 @@ namespace mont {
 namespace {
 
 constexpr size_t kAlign = 256;
-constexpr int kServeOrder = 2;   // software-pipelined job order (lag 32 products)
+constexpr int kServeOrder = 0;   // job order: column tiles, whole and small products, rows, output tiles
 
 // First-fit allocator over one device region, offsets in bytes.
 class Arena {
