@@ -80,6 +80,28 @@ def test_graph_replay_and_tuning_give_identical_results(m):
         assert np.array_equal(to_host(dc)[:wl.c_size], ref)
 
 
+def test_job_kind_boundaries(m):
+    """Shapes at the edges of each job kind: single-CTA products up to 2^13,
+    whole-product jobs for 2^14 and 2^15 (column levels computed while the
+    rows are staged, one operand possibly of length 1), column / row /
+    column jobs from 2^16 on; exact powers of two and lengths one past."""
+    shapes = [(4096, 4097), (8192, 1), (1, 8192), (8193, 1), (1, 12000), (16384, 1), (9000, 7385),
+              (1, 32768), (20000, 12769), (16385, 16384), (32768, 32769), (1, 40000), (40000, 3),
+              (65536, 65537), (70000, 1)]
+    primes = [synth.PRIMES[i % 3] for i in range(len(shapes))]
+    wl = synth.UnevenBatch(primes, [x for x, _ in shapes], [y for _, y in shapes], (604,))
+    for cfg in (None, (1, 0, 0), (3, 2, 1)):
+        import torch
+        da, db = to_dev(wl.a), to_dev(wl.b)
+        dc = torch.full((wl.c_size,), -1, dtype=torch.int32, device="cuda")
+        plan = m.PolymulBatchPlan.from_packed(wl.primes, da, wl.a_off, wl.la, db, wl.b_off, wl.lb, dc, wl.c_off)
+        if cfg is not None:
+            plan.config = m.PolymulBatchConfig(*cfg)
+        plan.run()
+        assert plan.status() == m.MONT_OK
+        assert np.array_equal(to_host(dc)[:wl.c_size], oracle_packed(wl)), cfg
+
+
 def test_alone_equals_in_the_mix(m):
     """Every product of a mixed batch equals the same product computed alone."""
     wl = mixed_batch(602)
