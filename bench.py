@@ -55,9 +55,9 @@ def parse_args():
     ap.add_argument("--log2n", type=int, default=28, help="elements per operand (default 2^28)")
     ap.add_argument("--batch-config", default=None,
                     help="uneven section: fixed launch shape CTAS_PER_SM,ORDER,KERNEL instead of autotuning")
-    ap.add_argument("--sections", default="uniform,reductions,uneven,serve",
-                    help="extra polymul sections to run (comma list of uniform, reductions, uneven, serve; "
-                         "empty for none)")
+    ap.add_argument("--sections", default="roundtrip,ntt,uniform,reductions,uneven,serve",
+                    help="extra sections to run (comma list of roundtrip, ntt, uniform, reductions, uneven, "
+                         "serve; empty for none)")
     ap.add_argument("--no-per-product", action="store_true",
                     help="skip the one-launch-per-product comparison of the uneven batch")
     return ap.parse_args()
@@ -354,6 +354,10 @@ def run_gpu(args, ws, rank, local):
         secs = [x for x in args.sections.split(",") if x]
         sampler2 = ClockSampler(bus)
         sampler2.start()
+        if "roundtrip" in secs:
+            extra["roundtrip_65536"] = bp.roundtrip_small(m, torch)
+        if "ntt" in secs:
+            extra["ntt_fwd_inv"] = bp.ntt_transforms(m, torch, peaks)
         if "uniform" in secs:
             extra["polymul_uniform_4096x2048"] = bp.uniform_batch(m, torch, peaks, cpu=not args.no_cpu_baseline)
         if "reductions" in secs:

@@ -107,6 +107,99 @@ def uniform_batch(m, torch, peaks, steps=20, warmup=3, cpu=True):
     return res
 
 
+def int_ops_ntt(n, inverse):
+    """Algorithmic integer lane-ops of one transform of size n (as in
+    int_ops_polymul): non-trivial CT butterflies 10, GS 9, twiddle-1
+    butterflies 4, plus the inverse's N^-1 scaling REDC (6) per element."""
+    levels = n.bit_length() - 1
+    trivial = n - 1
+    nontrivial = (n // 2) * levels - trivial
+    if inverse:
+        return 9 * nontrivial + 4 * trivial + 6 * n
+    return 10 * nontrivial + 4 * trivial
+
+
+def roundtrip_small(m, torch, steps=200, warmup=10):
+    """The 65,536-pair correctness workload as a latency figure: to_mont of a
+    and b, mont_mul, from_mont (four launches per step), P1."""
+    import oracle
+    p, a, b = synth.elementwise_small()
+    ctx = m.mont_setup(p)
+    da = torch.from_numpy(a.view(np.int32)).cuda()
+    db = torch.from_numpy(b.view(np.int32)).cuda()
+    am, bm, pm, out = (torch.empty_like(da) for _ in range(4))
+
+    def step():
+        m.to_mont(ctx, da, out=am)
+        m.to_mont(ctx, db, out=bm)
+        m.mont_mul(ctx, am, bm, out=pm)
+        m.from_mont(ctx, pm, out=out)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = _events(torch)
+    e0.record()
+    for _ in range(steps):
+        step()
+    e1.record()
+    e1.synchronize()
+    us = e0.elapsed_time(e1) / steps * 1e3
+    assert np.array_equal(out.cpu().numpy().view(np.uint32), oracle.mulmod_vec(p, a, b)), "round trip parity failed"
+    return {"workload": "65,536 pairs mod P1: to_mont a, to_mont b, mont_mul, from_mont (4 launches)",
+            "us_per_step": us, "us_per_launch": us / 4, "steps": steps, "warmup": warmup,
+            "l2": "operands (256 KiB each) stay in L2: a latency figure", "gpu_launches": 4 * steps,
+            "parity": "bit-exact against (a b) mod P"}
+
+
+def ntt_transforms(m, torch, peaks, steps=10, warmup=3):
+    """Stand-alone ntt_fwd / ntt_inv (natural order in and out): 4096 rows of
+    N = 4096 (one fused kernel each, L2 flushed before every launch) and 16
+    rows of N = 2^20 (column / row kernels and the bit-reversal), P1."""
+    import oracle
+    p = synth.P1
+    flush = torch.empty(64 << 20, dtype=torch.int32, device="cuda")
+    peak = int_peak_ops(peaks["sm_max_mhz"])
+    res = {}
+    for rows, logn in ((4096, 12), (16, 20)):
+        n = 1 << logn
+        x = synth.residues(rows * n, p, 900, logn).reshape(rows, n)
+        plan = m.ntt_plan_create(p, logn)
+        d = torch.from_numpy(x.view(np.int32)).cuda()
+        for _ in range(warmup):
+            m.ntt_fwd(plan, d)
+            m.ntt_inv(plan, d)
+        torch.cuda.synchronize()
+        evs = {"fwd": [], "inv": []}
+        for _ in range(steps):
+            for k, f in (("fwd", m.ntt_fwd), ("inv", m.ntt_inv)):
+                flush.fill_(1)
+                e0, e1 = _events(torch)
+                e0.record()
+                f(plan, d)
+                e1.record()
+                evs[k].append((e0, e1))
+        torch.cuda.synchronize()
+        assert torch.equal(d.cpu(), torch.from_numpy(x.view(np.int32))), "inverse(forward(x)) != x"
+        m.ntt_fwd(plan, d)
+        got0 = d[0].cpu().numpy().view(np.uint32)
+        assert np.array_equal(got0, oracle.ntt(p, x[0])), "ntt parity spot check failed"
+        r = {"rows": rows, "n": n, "unit": "Gcoef/s", "l2": "flushed (256 MiB write) before every launch",
+             "gpu_launches_per_call": 1 if logn <= 14 else 3}
+        for k in ("fwd", "inv"):
+            ms = float(np.mean([e0.elapsed_time(e1) for e0, e1 in evs[k]]))
+            ops = rows * int_ops_ntt(n, k == "inv")
+            r[k] = {"ms": ms, "value": rows * n / ms / 1e6,
+                    "roofline": {"bound": "alu", "achieved": ops / (ms / 1e3) / 1e12, "peak": peak / 1e12,
+                                 "unit": "Tops/s (integer lane-ops)", "frac": ops / (ms / 1e3) / peak},
+                    "hbm_gbs_at_pass_count": rows * n * 8 * (1 if logn <= 14 else 3) / (ms / 1e3) / 1e9}
+        res["N%d_x%d" % (n, rows)] = r
+        del d
+    del flush
+    res["parity"] = "inverse(forward(x)) == x for every row; row 0 of the forward equal to the oracle's NTT"
+    return res
+
+
 def reduction_ab(m, torch, steps=20, warmup=3):
     """Alg. 2 (REDC) against Alg. 3 (FourierREDC) as the twiddle, scaling and
     pointwise multiply of the same fused kernels: 4096 products of

@@ -58,9 +58,27 @@ k_ntt_fwd(NttArgs A)
     const bool valid = prod < A.batch;
     uint32_t *g = A.data + (valid ? prod * N : 0);
     const PadLayout lay[1] = {{smem + static_cast<size_t>(team) * PadLayout::words(N)}};
-    for (int k = tid; k < N; k += NT) lay[0][k] = valid ? g[k] : 0u;
-    __syncthreads();
-    fwd_passes<LOGN, NT, 1, true, 0, NP - 1>(lay, tid, A.tw, 0, 0, Mod{A.p, A.pp});
+    const Mod md{A.p, A.pp};
+    if constexpr (NP <= 1) {
+        for (int k = tid; k < N; k += NT) lay[0][k] = valid ? g[k] : 0u;
+        __syncthreads();
+        fwd_passes<LOGN, NT, 1, true, 0, NP - 1>(lay, tid, A.tw, 0, 0, md);
+    } else {
+        // pass 0 straight from global memory (a warp reads consecutive words)
+        using P0 = PassGeom<LOGN, NT, 0>;
+#pragma unroll
+        for (int r = 0; r < P0::GPT; r++) {
+            const int base = P0::base(tid, r);
+            uint32_t x[1][P0::G];
+#pragma unroll
+            for (int t = 0; t < P0::G; t++) x[0][t] = valid ? g[base + t * P0::HMIN] : 0u;
+            ct_group<P0::E, 1, true>(x, A.tw, 0, 0, md);
+#pragma unroll
+            for (int t = 0; t < P0::G; t++) elem(lay[0], base, t * P0::HMIN) = x[0][t];
+        }
+        __syncthreads();
+        fwd_passes<LOGN, NT, 1, true, 1, NP - 1>(lay, tid, A.tw, 0, 0, md);
+    }
     if (valid)
         for (int k = tid; k < N; k += NT) g[k] = csub(lay[0][A.bitrev ? k : brev<LOGN>(k)], A.p);
 }
@@ -78,11 +96,29 @@ k_ntt_inv(NttArgs A)
     const bool valid = prod < A.batch;
     uint32_t *g = A.data + (valid ? prod * N : 0);
     const PadLayout lay = {smem + static_cast<size_t>(team) * PadLayout::words(N)};
+    const Mod md{A.p, A.pp};
     for (int k = tid; k < N; k += NT) lay[A.bitrev ? k : brev<LOGN>(k)] = valid ? g[k] : 0u;
     __syncthreads();
-    inv_passes<LOGN, NT, true, NP - 1, 0>(lay, tid, A.tw, 0, 0, Mod{A.p, A.pp});
-    if (valid)
-        for (int k = tid; k < N; k += NT) g[k] = mont_mul(lay[k], A.ninv_mont, A.p, A.pp);
+    if constexpr (NP <= 1) {
+        inv_passes<LOGN, NT, true, NP - 1, 0>(lay, tid, A.tw, 0, 0, md);
+        if (valid)
+            for (int k = tid; k < N; k += NT) g[k] = mont_mul(lay[k], A.ninv_mont, A.p, A.pp);
+    } else {
+        inv_passes<LOGN, NT, true, NP - 1, 1>(lay, tid, A.tw, 0, 0, md);
+        // pass 0 scaled by N^-1 and stored straight to global memory
+        using P0 = PassGeom<LOGN, NT, 0>;
+#pragma unroll
+        for (int r = 0; r < P0::GPT; r++) {
+            const int base = P0::base(tid, r);
+            uint32_t y[1][P0::G];
+#pragma unroll
+            for (int t = 0; t < P0::G; t++) y[0][t] = elem(lay, base, t * P0::HMIN);
+            gs_group<P0::E, 1, true>(y, A.tw, 0, 0, md);
+            if (valid)
+#pragma unroll
+                for (int t = 0; t < P0::G; t++) g[base + t * P0::HMIN] = mont_mul(y[0][t], A.ninv_mont, A.p, A.pp);
+        }
+    }
 }
 
 template <int LOGN>

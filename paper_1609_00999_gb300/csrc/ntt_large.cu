@@ -198,21 +198,41 @@ k_row_ntt(RowNttArgs A, size_t prod0)
     for (int k = threadIdx.x; k < N2; k += NT) g[k] = INVERSE ? lay[0][k] : csub(lay[0][k], A.p);
 }
 
-// In-place bit-reversal permutation of each row of 2^log2n elements.
-__global__ void k_bitrev(uint32_t *data, int log2n, size_t batch)
+__device__ __forceinline__ int brev5(int x)
 {
-    const size_t n = size_t{1} << log2n, total = n * batch;
-    for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < total;
-         i += static_cast<size_t>(gridDim.x) * blockDim.x) {
-        const size_t row = i >> log2n;
-        const uint32_t j = static_cast<uint32_t>(i & (n - 1));
-        const uint32_t rj = __brev(j) >> (32 - log2n);
-        if (j < rj) {
-            uint32_t *g = data + row * n;
-            const uint32_t t = g[j];
-            g[j] = g[rj];
-            g[rj] = t;
-        }
+    return static_cast<int>(__brev(static_cast<unsigned>(x)) >> 27);
+}
+
+// In-place bit reversal of each row of 2^log2n elements (log2n >= 10) by
+// 32 x 32 tiles.  Index i = (a, b, c): a the top 5 bits, c the bottom 5, b
+// the log2n - 10 bits between; brev(i) = (brev5(c), brev(b), brev5(a)).  So
+// tile b (32 rows a of 32 consecutive words c, rows 2^(log2n-5) apart) and
+// tile brev(b) trade places with a transpose: one CTA per pair, both tiles
+// read before either is written.  Loads and stores move 128-byte row
+// segments; the padded shared-memory tiles make the transposed reads
+// conflict-free.
+__global__ void __launch_bounds__(256) k_bitrev_tiles(uint32_t *data, int log2n, size_t row0)
+{
+    __shared__ uint32_t t0[32][33], t1[32][33];
+    const int mb = log2n - 10;
+    const unsigned b = blockIdx.x;
+    const unsigned bb = mb > 0 ? (__brev(b) >> (32 - mb)) : 0u;
+    if (b > bb) return;                                  // the pair's other CTA does it
+    uint32_t *g = data + (row0 + blockIdx.y) * (size_t{1} << log2n);
+    const size_t rs = size_t{1} << (log2n - 5);
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const int a = ty + 8 * k;
+        t0[a][tx] = g[a * rs + (static_cast<size_t>(b) << 5) + tx];
+        t1[a][tx] = g[a * rs + (static_cast<size_t>(bb) << 5) + tx];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const int r = ty + 8 * k;                        // output row brev5(c), column tx = brev5(a)
+        g[r * rs + (static_cast<size_t>(bb) << 5) + tx] = t0[brev5(tx)][brev5(r)];
+        if (b != bb) g[r * rs + (static_cast<size_t>(b) << 5) + tx] = t1[brev5(tx)][brev5(r)];
     }
 }
 
@@ -327,13 +347,14 @@ int dispatch_row_ntt(int k2, const RowNttArgs &A, size_t count, cudaStream_t s)
 
 int launch_bitrev(uint32_t *data, int log2n, size_t batch, cudaStream_t s)
 {
-    const int sms = device_sm_count();
-    if (sms <= 0) return MONT_ECUDA;
-    const size_t total = (size_t{1} << log2n) * batch;
-    const size_t want = (total + 255) / 256;
-    const unsigned grid = static_cast<unsigned>(std::min<size_t>(want, static_cast<size_t>(sms) * 8));
-    k_bitrev<<<grid, 256, 0, s>>>(data, log2n, batch);
-    return launch_status();
+    if (log2n < 10) return MONT_EUNSUPPORTED;
+    const unsigned tiles = 1u << (log2n - 10);
+    for (size_t first = 0; first < batch; first += kMaxGridZ) {
+        const unsigned y = static_cast<unsigned>(std::min<size_t>(kMaxGridZ, batch - first));
+        k_bitrev_tiles<<<dim3(tiles, y), 256, 0, s>>>(data, log2n, first);
+        if (cudaGetLastError() != cudaSuccess) return MONT_ECUDA;
+    }
+    return MONT_OK;
 }
 
 }  // namespace
