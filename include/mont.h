@@ -222,11 +222,13 @@ typedef struct polymul_desc {
 } polymul_desc;
 
 /* Launch shape of a batch: CTAs per SM of the persistent grid (0 = as many
- * as fit), the job order (0: split products' column tiles first, then
- * the whole small products, then rows and output tiles; 1: small products
- * first; 2, 3: software-pipelined, rows of one product run beside the column
- * tiles of a later one, lag 32 or 64 products) and the kernel variant.
- * Chosen by polymul_batch_plan_tune. */
+ * as fit), the job order and the kernel variant.  Products up to 2^13 run
+ * whole in one CTA, products of 2^14 and 2^15 as one whole-product job each,
+ * larger ones as column-tile, row and output-tile jobs.  Orders: 0: column
+ * tiles first, then whole-product and small jobs, then rows and output
+ * tiles; 1: whole-product and small jobs first; 2, 3: software-pipelined,
+ * rows of one product beside the column tiles of a later one, lag 32 or 64
+ * products.  Chosen by polymul_batch_plan_tune. */
 typedef struct polymul_batch_config {
     int ctas_per_sm;
     int order;
