@@ -243,6 +243,20 @@ typedef struct polymul_batch_config {
 typedef struct polymul_batch_plan polymul_batch_plan;
 
 int polymul_batch_plan_create(const polymul_desc *descs, size_t count, polymul_batch_plan **out);
+
+/* Host only, no device work: the job list the batch kernel runs for these
+ * descriptors in job order `order` (0 .. 3), for inspection and tests.  The
+ * first min(cap, *njobs) jobs go to jobs, 4 words each: kind (0: single-CTA
+ * products, the job covering `count` consecutive products; 1: column tile;
+ * 2: row; 3: output tile; 4: whole product), log2 N, product, and the tile
+ * or row index (kind 0: the product count).  Products are numbered in the
+ * kernel's order (single-CTA products first, by size, then the others in
+ * descriptor order); prods, if not NULL, receives 3 words per product:
+ * log2 N, column tiles, rows.  *njobs gets the full job count.  Errors as
+ * polymul_batch_plan_create's descriptor checks; MONT_EINVAL for a bad
+ * order. */
+int polymul_batch_describe(const polymul_desc *descs, size_t count, int order, uint32_t *jobs, size_t cap,
+                           uint32_t *prods, size_t *njobs);
 void polymul_batch_plan_destroy(polymul_batch_plan *plan);
 size_t polymul_batch_plan_workspace_bytes(const polymul_batch_plan *plan);
 int polymul_batch_plan_get_config(const polymul_batch_plan *plan, polymul_batch_config *cfg);

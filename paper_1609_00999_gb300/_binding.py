@@ -119,6 +119,9 @@ class PolymulBatchConfig(ctypes.Structure):
 def _declare_batch(L):
     vpp = ctypes.POINTER(_vp)
     L.polymul_batch_plan_create.argtypes = [ctypes.POINTER(PolymulDesc), _sz, vpp]
+    L.polymul_batch_describe.argtypes = [ctypes.POINTER(PolymulDesc), _sz, ctypes.c_int, _vp, _sz, _vp,
+                                         ctypes.POINTER(_sz)]
+    L.polymul_batch_describe.restype = ctypes.c_int
     L.polymul_batch_plan_destroy.argtypes = [_vp]
     L.polymul_batch_plan_destroy.restype = None
     L.polymul_batch_plan_workspace_bytes.argtypes = [_vp]
@@ -482,6 +485,24 @@ class PolymulBatchPlan:
 
 def polymul_batch_plan_create(descs, keepalive=()):
     return PolymulBatchPlan(descs, keepalive)
+
+
+def polymul_batch_describe(descs, order):
+    """Host only: (jobs [n][4] uint32: kind, log2 N, product, index;
+    prods [count][3] uint32: log2 N, column tiles, rows) of the job list the
+    batch kernel runs for these descriptors in job order `order`."""
+    import numpy as np
+    arr = (PolymulDesc * max(1, len(descs)))()
+    for i, d in enumerate(descs):
+        arr[i] = d
+    n = _sz(0)
+    _check(lib().polymul_batch_describe(arr, len(descs), int(order), None, 0, None, ctypes.byref(n)),
+           "polymul_batch_describe")
+    jobs = np.zeros((max(1, n.value), 4), dtype=np.uint32)
+    prods = np.zeros((max(1, len(descs)), 3), dtype=np.uint32)
+    _check(lib().polymul_batch_describe(arr, len(descs), int(order), jobs.ctypes.data, n.value, prods.ctypes.data,
+                                        ctypes.byref(n)), "polymul_batch_describe")
+    return jobs[:n.value], prods[:len(descs)]
 
 
 # numpy mirrors of mont_request / mont_completion (48 and 16 bytes)

@@ -713,6 +713,34 @@ int launch(polymul_batch_plan *pl, const polymul_batch_config &cfg, cudaStream_t
 }  // namespace
 }  // namespace mont
 
+extern "C" int polymul_batch_describe(const polymul_desc *descs, size_t count, int order, uint32_t *jobs,
+                                      size_t cap, uint32_t *prods, size_t *njobs)
+{
+    using namespace mont;
+    if (!njobs || (count && !descs) || order < 0 || order >= kJobOrders || (cap && !jobs)) return MONT_EINVAL;
+    if (count > (size_t{1} << 31)) return MONT_ERANGE;
+    BatchHost host;
+    std::vector<uint32_t> prime_list;
+    std::vector<int> prime_log2;
+    const int rc = batch_build(descs, count, host, prime_list, prime_log2, false);
+    if (rc != MONT_OK) return rc;
+    const std::vector<Job> &list = host.jobs[order];
+    *njobs = list.size();
+    for (size_t i = 0; i < list.size() && i < cap; i++) {
+        jobs[4 * i] = list[i].type;
+        jobs[4 * i + 1] = list[i].k;
+        jobs[4 * i + 2] = list[i].prod;
+        jobs[4 * i + 3] = list[i].idx;
+    }
+    if (prods)
+        for (size_t i = 0; i < host.prods.size(); i++) {
+            prods[3 * i] = host.prods[i].k;
+            prods[3 * i + 1] = host.prods[i].ntiles;
+            prods[3 * i + 2] = host.prods[i].nrows;
+        }
+    return MONT_OK;
+}
+
 extern "C" int polymul_batch_plan_create(const polymul_desc *descs, size_t count, polymul_batch_plan **out)
 {
     using namespace mont;

@@ -1,0 +1,108 @@
+"""Host-side job lists of the persistent batch kernel (no GPU needed).
+
+The kernel's progress rests on one property of its job list: every job
+waits only on jobs earlier in the list (a row job on all column tiles of
+its product, an output-tile job on all rows of its product), so the
+earliest unfinished job can always run.  These tests build the job lists
+for every job order from the host builder the kernel uses and check that
+property, that every product is covered exactly once by jobs of the kind
+its size calls for, and the descriptor checks."""
+import pytest
+
+from paper_1609_00999_gb300 import build as gbuild
+from paper_1609_00999_gb300 import synth
+
+SMALL, COLF, ROW, COLI, WHOLE = 0, 1, 2, 3, 4
+
+
+@pytest.fixture(scope="module")
+def m():
+    gbuild.build()
+    import paper_1609_00999_gb300 as m
+    return m
+
+
+def fake_descs(m, la, lb, primes):
+    """Descriptors with distinct, non-overlapping addresses that the host
+    builder only compares, never dereferences."""
+    out, base = [], 1 << 40
+    for x, y, p in zip(la, lb, primes):
+        a, b, c = base, base + 4 * int(x), base + 4 * (int(x) + int(y))
+        base += 4 * (2 * (int(x) + int(y))) + 4096
+        out.append(m.PolymulDesc(a, b, c, int(x), int(y), int(p), 0))
+    return out
+
+
+def check_job_list(jobs, prods):
+    count = len(prods)
+    small = [0] * count
+    whole = [0] * count
+    colf, row, coli = [0] * count, [0] * count, [0] * count
+    for kind, k, prod, idx in jobs.tolist():
+        if kind == SMALL:
+            assert idx >= 1 and prod + idx <= count
+            for q in range(prod, prod + idx):
+                assert prods[q][0] == k and k <= 13
+                small[q] += 1
+        elif kind == WHOLE:
+            assert prods[prod][0] == k and 14 <= k <= 15
+            whole[prod] += 1
+        elif kind == COLF:
+            assert prods[prod][0] == k >= 16 and idx < prods[prod][1]
+            colf[prod] += 1
+        elif kind == ROW:
+            assert colf[prod] == prods[prod][1], "row job before all column tiles of its product"
+            assert idx < prods[prod][2]
+            row[prod] += 1
+        elif kind == COLI:
+            assert row[prod] == prods[prod][2], "output tile before all rows of its product"
+            assert idx < prods[prod][1]
+            coli[prod] += 1
+        else:
+            raise AssertionError("unknown job kind %d" % kind)
+    for q in range(count):
+        k, ntiles, nrows = (int(v) for v in prods[q])
+        if k <= 13:
+            assert small[q] == 1 and whole[q] == colf[q] == row[q] == coli[q] == 0, q
+        elif k <= 15:
+            assert whole[q] == 1 and small[q] == colf[q] == row[q] == coli[q] == 0, q
+        else:
+            assert (colf[q], row[q], coli[q]) == (ntiles, nrows, ntiles) and small[q] == whole[q] == 0, q
+            assert nrows == 1 << (k - 13)
+
+
+@pytest.mark.parametrize("order", [0, 1, 2, 3])
+def test_uneven_workload_job_lists(m, order):
+    """The 10,000-product uneven workload (sizes and primes only)."""
+    lens = synth.loguniform_lengths(10000, 1 << 6, 1 << 16, synth.SEED_BATCH_UNEVEN, 0)
+    primes = synth.choose_primes(10000, synth.SEED_BATCH_UNEVEN, 1)
+    jobs, prods = m.polymul_batch_describe(fake_descs(m, lens, lens, primes), order)
+    check_job_list(jobs, prods)
+
+
+@pytest.mark.parametrize("order", [0, 1, 2, 3])
+def test_mixed_sizes_job_lists(m, order):
+    """Every size 2^0 .. 2^21, asymmetric operands, primes mixed."""
+    la, lb = [], []
+    for k in range(22):
+        n = 1 << k
+        la += [max(1, n // 2), 1, max(1, n // 4)]
+        lb += [max(1, n // 2), max(1, n - 1), max(1, n // 2 + 1)]
+    primes = [synth.PRIMES[i % 3] for i in range(len(la))]
+    jobs, prods = m.polymul_batch_describe(fake_descs(m, la, lb, primes), order)
+    check_job_list(jobs, prods)
+    assert {int(p[0]) for p in prods} >= set(range(0, 22))
+
+
+def test_describe_rejects_bad_input(m):
+    d = fake_descs(m, [10], [10], [synth.P1])
+    with pytest.raises(m.MontError):
+        m.polymul_batch_describe(d, 4)                       # no such order
+    big = fake_descs(m, [1 << 21], [1 << 21], [synth.P1])    # N = 2^22 > 2^21
+    with pytest.raises(m.MontError) as e:
+        m.polymul_batch_describe(big, 0)
+    assert e.value.code == m.MONT_EUNSUPPORTED
+    zero = fake_descs(m, [0], [5], [synth.P1])
+    with pytest.raises(m.MontError) as e:
+        m.polymul_batch_describe(zero, 0)
+    assert e.value.code == m.MONT_EINVAL
