@@ -361,6 +361,7 @@ def run_gpu(args, ws, rank, local):
         if "uniform" in secs:
             extra["polymul_uniform_4096x2048"] = bp.uniform_batch(m, torch, peaks, cpu=not args.no_cpu_baseline)
         if "reductions" in secs:
+            extra["reductions_elementwise_2e28"] = bp.reductions_elementwise(m, torch, peaks)
             extra["polymul_alg2_vs_alg3_4096x2048"] = bp.reduction_ab(m, torch)
         if "uneven" in secs:
             cfg = tuple(int(x) for x in args.batch_config.split(",")) if args.batch_config else None

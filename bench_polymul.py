@@ -200,6 +200,50 @@ def ntt_transforms(m, torch, peaks, steps=10, warmup=3):
     return res
 
 
+def reductions_elementwise(m, torch, peaks, log2n=28, steps=10, warmup=3):
+    """The three reductions of Sec. 3.1 on the same vectors: Barrett (Alg. 1,
+    a b mod P on plain residues), REDC (Alg. 2) and FourierREDC (Alg. 3, a b
+    R^-1 mod P), 2^log2n residues per operand mod P2 = 469762049 (the prime
+    all three accept).  12 B per element: HBM-bound unless a reduction's
+    arithmetic outruns the memory time."""
+    import oracle
+    p = synth.P2
+    n = 1 << log2n
+    a = synth.residues(n, p, 950, 0)
+    b = synth.residues(n, p, 950, 1)
+    da = torch.from_numpy(a.view(np.int32)).cuda()
+    db = torch.from_numpy(b.view(np.int32)).cuda()
+    out = torch.empty_like(da)
+    ctx = m.mont_setup(p)
+    fns = {"alg1_barrett": lambda: m.barrett_mulmod(p, da, db, out=out),
+           "alg2_redc": lambda: m.mont_mul(ctx, da, db, out=out),
+           "alg3_fourier_redc": lambda: m.fourier_redc_mul(ctx, da, db, out=out)}
+    res = {"workload": "2^%d residues per operand mod 469762049, one elementwise multiply" % log2n,
+           "unit": "Gmulmod/s", "steps": steps, "warmup": warmup, "bytes_per_element": 12,
+           "l2": "operands larger than L2; no flush", "gpu_launches": steps * len(fns)}
+    sample = np.arange(0, n, 4099, dtype=np.int64)
+    for k, f in fns.items():
+        for _ in range(warmup):
+            f()
+        torch.cuda.synchronize()
+        e0, e1 = _events(torch)
+        e0.record()
+        for _ in range(steps):
+            f()
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        got = out.cpu().numpy().view(np.uint32)[sample]
+        ref = (oracle.mulmod_vec(p, a[sample], b[sample]) if k == "alg1_barrett"
+               else oracle.mont_mul(p, a[sample], b[sample]))
+        assert np.array_equal(got, ref), "%s parity spot check failed" % k
+        res[k] = {"ms": ms, "value": n / ms / 1e6, "hbm_gbs": 12 * n / ms / 1e6,
+                  "hbm_frac": 12 * n / ms / 1e6 / peaks["hbm_gbs"]}
+    del da, db, out
+    torch.cuda.empty_cache()
+    return res
+
+
 def reduction_ab(m, torch, steps=20, warmup=3):
     """Alg. 2 (REDC) against Alg. 3 (FourierREDC) as the twiddle, scaling and
     pointwise multiply of the same fused kernels: 4096 products of
