@@ -9,11 +9,13 @@
 
 namespace mont {
 
-// Threads per transform of 2^LOGN elements (16 elements per thread per array).
+// Threads per transform of 2^LOGN elements: 16 elements per thread per
+// array, except 2^13 on 256 threads (32 per thread, a radix-32 first pass),
+// which fits three CTAs and 24 warps per SM where 512 threads fit one.
 template <int LOGN>
 constexpr int nt_of()
 {
-    return LOGN <= 4 ? 1 : (1 << (LOGN - 4));
+    return LOGN <= 4 ? 1 : (LOGN == 13 ? 256 : (1 << (LOGN - 4)));
 }
 
 // Transforms per CTA for the single-CTA kernels (256-thread CTAs below 2^12).
@@ -24,12 +26,13 @@ constexpr int teams_of()
 }
 
 // CTAs per SM the register budget is sized for: four 256-thread CTAs
-// (64 registers per thread, no spills) for the fused products up to 2^12;
-// one CTA for the 512- and 1024-thread transforms.
+// (64 registers per thread, no spills) for the fused products up to 2^12,
+// three for 2^13 (their 66 KB of shared memory fits three); one CTA for the
+// 1024-thread 2^14 transforms.
 template <int LOGN>
 constexpr int min_ctas_of()
 {
-    return teams_of<LOGN>() * nt_of<LOGN>() <= 256 ? 4 : 1;
+    return teams_of<LOGN>() * nt_of<LOGN>() <= 256 ? (LOGN >= 13 ? 3 : 4) : 1;
 }
 
 // Shared-memory words one team needs for a product of 2^LOGN (both operands,
