@@ -10,12 +10,14 @@
 namespace mont {
 
 // Threads per transform of 2^LOGN elements: 16 elements per thread per
-// array, except 2^13 on 256 threads (32 per thread, a radix-32 first pass),
-// which fits three CTAs and 24 warps per SM where 512 threads fit one.
+// array, except 2^13 on 256 threads and 2^14 on 512 (32 per thread, a
+// radix-32 first pass): 2^13 then fits three CTAs and 24 warps per SM where
+// 512 threads fit one, and 2^14 (one CTA per SM by its 132 KB of shared
+// memory either way) gets up to 128 registers per thread.
 template <int LOGN>
 constexpr int nt_of()
 {
-    return LOGN <= 4 ? 1 : (LOGN == 13 ? 256 : (1 << (LOGN - 4)));
+    return LOGN <= 4 ? 1 : (LOGN == 13 ? 256 : (LOGN == 14 ? 512 : (1 << (LOGN - 4))));
 }
 
 // Transforms per CTA for the single-CTA kernels (256-thread CTAs below 2^12).
@@ -28,7 +30,7 @@ constexpr int teams_of()
 // CTAs per SM the register budget is sized for: four 256-thread CTAs
 // (64 registers per thread, no spills) for the fused products up to 2^12,
 // three for 2^13 (their 66 KB of shared memory fits three); one CTA for the
-// 1024-thread 2^14 transforms.
+// 512-thread 2^14 transforms.
 template <int LOGN>
 constexpr int min_ctas_of()
 {
