@@ -19,10 +19,15 @@
 //
 // Register passes: each thread holds a group of 2^E elements at stride
 // HMIN = N / 2^(S0+E) and applies levels S0 .. S0+E-1 to it in registers
-// (radix 2^E); passes exchange data through shared memory.  Shared-memory
-// index j is stored at swz(j), an XOR swizzle of the low five bits that keeps
-// the strided group accesses of every pass (nearly) free of bank conflicts
-// and never leaves the aligned 32-word segment (identity for j < 16).
+// (radix 2^E, E <= 4, or 5 when a thread holds 32 or more elements); passes
+// exchange data through shared memory.  A whole transform lives at word
+// j + (j >> 5) (PadLayout: compile-time offsets within a group, at most
+// 2-way bank conflicts); column tiles use an XOR layout per column
+// (ColLayout, optionally on top of the swizzle swz).
+//
+// Reductions: REDC (Alg. 2) everywhere by default; FourierREDC (Alg. 3) as
+// the RedAlg3 policy for the reduction comparison.  Forward values stay
+// lazily in [0, 2P) (see below), inverse values in [0, P).
 #pragma once
 #include <cstdint>
 
