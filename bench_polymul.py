@@ -48,6 +48,23 @@ def int_ops_polymul(n, la, lb):
     return fwd + inv + 6 * n + 6 * lb
 
 
+def batch_hbm_bytes(n, la, lb):
+    """Algorithmic HBM bytes of one product of size n in the batch kernel:
+    operands in and result out; products of 2^14 and 2^15 (whole-product
+    jobs) also read their operands once per row (2 or 4 rows) and pass their
+    product rows through scratch (n words out and back); larger ones move
+    2n words of forward scratch out and back, n words of product rows out
+    and back."""
+    lc = la + lb - 1
+    io = 4 * (la + lb + lc)
+    if n <= 1 << 13:
+        return io
+    if n <= 1 << 15:
+        rows = n >> 13
+        return io + 4 * (rows - 1) * (la + lb) + 4 * 2 * n
+    return io + 4 * (2 * 2 * n + 2 * n)
+
+
 def _events(torch):
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
@@ -316,6 +333,7 @@ def uneven_batch(m, torch, peaks, steps=10, warmup=3, cpu=True, per_product=True
     ns = [1 << int(lc - 1).bit_length() for lc in (wl.la + wl.lb - 1)]
     ops = float(sum(int_ops_polymul(n, int(la), int(lb)) for n, la, lb in zip(ns, wl.la, wl.lb)))
     peak = int_peak_ops(peaks["sm_max_mhz"])
+    hbm = float(sum(batch_hbm_bytes(n, int(la), int(lb)) for n, la, lb in zip(ns, wl.la, wl.lb)))
     res = {"workload": "10,000 products, L log-uniform in [2^6, 2^16], primes uniform from "
                        "{2013265921, 469762049, 754974721}, N padded to powers of two",
            "value": coeffs / ms / 1e6, "unit": "Gcoef/s", "ms": ms, "steps": steps, "warmup": warmup,
@@ -326,7 +344,12 @@ def uneven_batch(m, torch, peaks, steps=10, warmup=3, cpu=True, per_product=True
            "gpu_launches": steps,
            "roofline": {"bound": "alu", "kernel": "k_polymul_batch", "achieved": ops / (ms / 1e3) / 1e12,
                         "peak": peak / 1e12, "unit": "Tops/s (integer lane-ops)", "frac": ops / (ms / 1e3) / peak,
-                        "algorithmic_ops": ops, "traffic": None}}
+                        "algorithmic_ops": ops, "traffic": None},
+           "hbm_at_pass_count": {"bytes": hbm, "achieved_gbs": hbm / (ms / 1e3) / 1e9, "peak_gbs": peaks["hbm_gbs"],
+                                 "frac": hbm / (ms / 1e3) / 1e9 / peaks["hbm_gbs"],
+                                 "passes": "one for N <= 2^13; operands, results and the product rows' scratch "
+                                           "round trip for 2^14 and 2^15 (operands read 2 or 4 times); "
+                                           "three passes through 2N words of scratch above"}}
     # spot check a few products against the oracle
     got = dc.cpu().numpy().view(np.uint32)
     for i in (0, 1, 9999):
