@@ -1,0 +1,74 @@
+"""Host-side checks of the bench's work accounting (no GPU).
+
+The roofline figures divide algorithmic work by kernel time, so the counts
+must describe the transform the kernels run: levels 0 .. K-1 of a
+Cooley-Tukey forward transform over 2^l blocks of size N / 2^l, block i
+multiplying by w^(brev_l(i) N / 2^(l+1)), output in bit-reversed order
+(Sec. 4: the twiddle multiply is the REDC of Alg. 2).  The brute-force walk
+below runs that transform, checks it against the DFT, and counts its
+butterflies by whether the twiddle is 1.
+"""
+import numpy as np
+import pytest
+
+import bench_polymul as bp
+import oracle
+from paper_1609_00999_gb300 import synth
+
+
+def _brev(i, bits):
+    return int(format(i, f"0{bits}b")[::-1], 2) if bits else 0
+
+
+def _ct_forward_counting(p, x):
+    n = len(x)
+    k = n.bit_length() - 1
+    w = int(oracle.root_of_unity(p, n))
+    a = [int(v) for v in x]
+    trivial = nontrivial = 0
+    for level in range(k):
+        half = n >> (level + 1)
+        for blk in range(1 << level):
+            tw = pow(w, _brev(blk, level) * half, p)
+            base = blk * 2 * half
+            for j in range(base, base + half):
+                u, v = a[j], a[j + half] * tw % p
+                a[j], a[j + half] = (u + v) % p, (u - v) % p
+                if tw == 1:
+                    trivial += 1
+                else:
+                    nontrivial += 1
+    return a, trivial, nontrivial
+
+
+@pytest.mark.parametrize("k", range(1, 11))
+def test_butterfly_classes_match_op_count(k):
+    n = 1 << k
+    p = synth.P1
+    x = synth.residues(n, p, 4242, k)
+    y, trivial, nontrivial = _ct_forward_counting(p, x)
+    ref = oracle.dft(p, x)
+    assert [y[_brev(i, k)] for i in range(n)] == [int(v) for v in ref]
+    assert trivial == n - 1
+    assert trivial + nontrivial == (n // 2) * k
+    assert bp.int_ops_ntt(n, False) == 10 * nontrivial + 4 * trivial
+    assert bp.int_ops_ntt(n, True) == 9 * nontrivial + 4 * trivial + 6 * n
+    la, lb = n // 2, n // 2
+    assert bp.int_ops_polymul(n, la, lb) == (2 * (10 * nontrivial + 4 * trivial) + 9 * nontrivial + 4 * trivial
+                                             + 6 * n + 6 * lb)
+
+
+def test_batch_hbm_bytes_pass_structure():
+    # One pass for products held in one CTA.
+    assert bp.batch_hbm_bytes(1 << 13, 4000, 4000) == 4 * (4000 + 4000 + 7999)
+    # 2^14 / 2^15: operands re-read once per extra row, product rows out and back.
+    io = 4 * (9000 + 8000 + 16999)
+    assert bp.batch_hbm_bytes(1 << 15, 9000, 8000) == io + 4 * 3 * 17000 + 8 * (1 << 15)
+    # Larger: forward scratch (2N) and product rows (N) each out and back.
+    n = 1 << 17
+    io = 4 * (70000 + 60000 + 129999)
+    assert bp.batch_hbm_bytes(n, 70000, 60000) == io + 4 * 6 * n
+    lens = np.array([1 << 12, 1 << 14, 1 << 16])
+    sizes = [1 << int(2 * L - 2).bit_length() for L in lens]
+    vals = [bp.batch_hbm_bytes(s, int(L), int(L)) for s, L in zip(sizes, lens)]
+    assert vals == sorted(vals)
