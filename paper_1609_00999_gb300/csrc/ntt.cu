@@ -60,7 +60,7 @@ k_ntt_fwd(NttArgs A)
     const PadLayout lay[1] = {{smem + static_cast<size_t>(team) * PadLayout::words(N)}};
     const Mod md{A.p, A.pp};
     if constexpr (NP <= 1) {
-        for (int k = tid; k < N; k += NT) lay[0][k] = valid ? g[k] : 0u;
+        stage_in<N, NT>(lay[0], g, tid, valid, [](int k) { return k; });
         __syncthreads();
         fwd_passes<LOGN, NT, 1, true, 0, NP - 1>(lay, tid, A.tw, 0, 0, md);
     } else {
@@ -97,7 +97,8 @@ k_ntt_inv(NttArgs A)
     uint32_t *g = A.data + (valid ? prod * N : 0);
     const PadLayout lay = {smem + static_cast<size_t>(team) * PadLayout::words(N)};
     const Mod md{A.p, A.pp};
-    for (int k = tid; k < N; k += NT) lay[A.bitrev ? k : brev<LOGN>(k)] = valid ? g[k] : 0u;
+    const int bitrev = A.bitrev;
+    stage_in<N, NT>(lay, g, tid, valid, [bitrev](int k) { return bitrev ? k : brev<LOGN>(k); });
     __syncthreads();
     if constexpr (NP <= 1) {
         inv_passes<LOGN, NT, true, NP - 1, 0>(lay, tid, A.tw, 0, 0, md);

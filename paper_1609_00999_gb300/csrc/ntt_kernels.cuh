@@ -88,6 +88,23 @@ __device__ __forceinline__ uint32_t load_operand(const uint32_t *p)
     else return *p;
 }
 
+// Copies the N words of g into a shared-memory layout, word k to position
+// at(k), k = tid + i NT.  Every load of the thread is issued before its first
+// store, so each thread has N / NT loads in flight (a loop that stores each
+// word as it arrives waits out one memory latency per word).  Zeros when
+// !valid.
+template <int N, int NT, class L, class AT>
+__device__ __forceinline__ void stage_in(const L &lay, const uint32_t *g, int tid, bool valid, AT at)
+{
+    static_assert(N % NT == 0, "the thread count divides the transform");
+    constexpr int PER = N / NT;
+    uint32_t v[PER];
+#pragma unroll
+    for (int i = 0; i < PER; i++) v[i] = valid ? g[tid + i * NT] : 0u;
+#pragma unroll
+    for (int i = 0; i < PER; i++) lay[at(tid + i * NT)] = v[i];
+}
+
 // Operand source of a product: element j (< 2^LOGN) of operand 0 (a) or 1
 // (b), zero at and beyond the operand's length, b multiplied by k_scale
 // through the reduction (b N^-1 R^2 R^-1 = b N^-1 R).

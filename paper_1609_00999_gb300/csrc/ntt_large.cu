@@ -191,7 +191,7 @@ k_row_ntt(RowNttArgs A, size_t prod0)
     const int r = blockIdx.x;
     uint32_t *g = A.data + prod * A.n + (static_cast<size_t>(r) << K2);
     const PadLayout lay[1] = {{smem}};
-    for (int k = threadIdx.x; k < N2; k += NT) lay[0][k] = g[k];
+    stage_in<N2, NT>(lay[0], g, threadIdx.x, true, [](int k) { return k; });
     __syncthreads();
     if constexpr (!INVERSE) fwd_passes<K2, NT, 1, false, 0, NP - 1>(lay, threadIdx.x, A.tw, A.k1, r, Mod{A.p, A.pp});
     else inv_passes<K2, NT, false, NP - 1, 0>(lay[0], threadIdx.x, A.tw, A.k1, r, Mod{A.p, A.pp});
@@ -297,8 +297,8 @@ int launch_row_ntt(const RowNttArgs &A, size_t count, cudaStream_t s)
 
 // Row levels K2: 2^12 rows up to N = 2^16; rows of 2^13 and 2^14 for
 // N = 2^17 and 2^18, which keeps four column levels (register column
-// passes); beyond, 2^12 rows again (rows of 2^14 run one 1024-thread CTA per
-// SM and lose to more column levels) until K - 10 > 12.
+// passes); beyond, 2^12 rows again (rows of 2^14, one CTA per SM, measured
+// no faster there) until K - 10 > 12.
 int split_k2(int k)
 {
     if (k <= 16) return 12;
