@@ -102,6 +102,19 @@ int barrett_mulmod(uint32_t p, const uint32_t *a, const uint32_t *b, uint32_t *o
 int fourier_redc_mul(const mont_ctx *ctx, const uint32_t *a, const uint32_t *b, uint32_t *out, size_t n,
                      cudaStream_t stream);
 
+/*
+ * Checks the precondition every entry point states for its inputs: REDC
+ * (Alg. 2) and the transforms take residues of Z_P (Sec. 3.1), so each word
+ * must lie in [0, p).  Returns MONT_OK if x[i] < p for every i < n (and for
+ * n == 0), MONT_ERANGE if some word is >= p, MONT_EINVAL for p even, p < 3,
+ * p >= 2^31, or x NULL with n > 0.  One read of x (4 B per element).
+ * Unlike every other call it is SYNCHRONOUS: it runs on `stream` after the
+ * work queued there, reads the verdict back and returns once the stream has
+ * drained.  A debugging aid for callers whose data did not come from this
+ * library; the product calls never run it.
+ */
+int mont_check_residues(uint32_t p, const uint32_t *x, size_t n, cudaStream_t stream);
+
 /* ------------------------------------------------------------------------
  * Number-theoretic transform and polynomial multiplication.
  *

@@ -14,4 +14,4 @@ from ._binding import polymul_many_fourier  # noqa: F401
 from ._binding import (PolymulBatchConfig, PolymulBatchPlan, PolymulDesc,  # noqa: F401
                        polymul_batch_describe, polymul_batch_plan_create)
 from ._binding import MontServer, MontServerStats, completion_dtype, request_dtype  # noqa: F401
-from ._binding import barrett_mulmod, fourier_redc_mul  # noqa: F401
+from ._binding import barrett_mulmod, check_residues, fourier_redc_mul  # noqa: F401

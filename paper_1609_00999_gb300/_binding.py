@@ -69,6 +69,8 @@ def _declare(L):
     L.mont_fma.argtypes = [ctxp, _vp, _vp, _vp, _vp, _sz, _vp]
     L.barrett_mulmod.argtypes = [ctypes.c_uint32, _vp, _vp, _vp, _sz, _vp]
     L.fourier_redc_mul.argtypes = [ctxp, _vp, _vp, _vp, _sz, _vp]
+    L.mont_check_residues.argtypes = [ctypes.c_uint32, _vp, _sz, _vp]
+    L.mont_check_residues.restype = ctypes.c_int
     for name in ("mont_setup", "to_mont", "from_mont", "mont_mul", "mont_fma", "barrett_mulmod",
                  "fourier_redc_mul"):
         getattr(L, name).restype = ctypes.c_int
@@ -280,6 +282,16 @@ def fourier_redc_mul(ctx, a, b, out=None, stream=None):
     _check(lib().fourier_redc_mul(ctypes.byref(ctx), _dev_ptr(a, "a"), _dev_ptr(b, "b"), _dev_ptr(out, "out"),
                                   a.numel(), _stream_handle(stream, a.device)), "fourier_redc_mul")
     return out
+
+
+def check_residues(p, x, stream=None):
+    """True if every word of x lies in [0, p), False if some word is >= p
+    (a synchronous device-side check of the inputs' precondition)."""
+    rc = lib().mont_check_residues(int(p), _dev_ptr(x, "x"), x.numel(), _stream_handle(stream, x.device))
+    if rc == MONT_ERANGE:
+        return False
+    _check(rc, "mont_check_residues")
+    return True
 
 
 NTT_BITREV = 1

@@ -57,6 +57,11 @@ def test_host_side_argument_errors(L):
     assert L.mont_mul(ctypes.byref(ctx), None, None, None, 0, None) == m.MONT_OK
     assert L.mont_fma(ctypes.byref(ctx), buf, buf, None, buf, 4, None) == m.MONT_EINVAL
     assert L.to_mont(None, buf, buf, 4, None) == m.MONT_EINVAL
+    # the residue check: bad moduli and a NULL buffer fail before any device work
+    for p in (0, 1, 2, 4, 2 ** 31, 2 ** 32 - 1):
+        assert L.mont_check_residues(p, buf, 4, None) == m.MONT_EINVAL
+    assert L.mont_check_residues(synth.P1, None, 4, None) == m.MONT_EINVAL
+    assert L.mont_check_residues(synth.P1, None, 0, None) == m.MONT_OK
     for code in (0, -1, -2, -3, -4, -5, -6, -99):
         assert isinstance(m.strerror(code), str)
 

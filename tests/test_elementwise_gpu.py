@@ -159,3 +159,40 @@ def test_pinned_host_operands_zero_copy(m):
     dout = torch.empty(n, dtype=torch.int32, device="cuda")
     m.mont_mul(ctx, ha, to_dev(b), out=dout)                   # host and device operands mixed
     assert np.array_equal(to_host(dout), oracle.mont_mul(p, a, b))
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 31, 1023, 4097, 65537, (1 << 22) + 3])
+@pytest.mark.parametrize("p", synth.PRIMES)
+def test_check_residues(m, p, n):
+    """mont_check_residues agrees with the definition (every word < p) on
+    aligned and misaligned buffers, with one planted non-residue at the head,
+    the middle or the ragged tail, and with the largest residue p - 1."""
+    import torch
+    x = synth.residues(n + 1, p, 210, n)
+    d = to_dev(x)
+    for view in (d[:n], d[1:n + 1]):                           # 16-byte aligned, then 4 bytes off
+        assert m.check_residues(p, view)
+        for pos in sorted({0, n // 2, n - 1}):
+            for bad in (p, 0xFFFFFFFF):
+                host = view.cpu().numpy().view(np.uint32).copy()
+                host[pos] = bad
+                v2 = view.clone() if view.data_ptr() % 16 == 0 else d.clone()[1:n + 1]
+                v2.copy_(torch.from_numpy(host.view(np.int32)))
+                assert not (host < p).all()
+                assert not m.check_residues(p, v2), (pos, bad)
+    top = torch.full((n,), p - 1, dtype=torch.int32, device="cuda")
+    assert m.check_residues(p, top)
+    assert m.check_residues(p, torch.empty(0, dtype=torch.int32, device="cuda"))
+
+
+def test_check_residues_pinned_and_errors(m):
+    import torch
+    p = synth.P2
+    x = synth.residues(70001, p, 211, 0)
+    h = torch.from_numpy(x.view(np.int32)).pin_memory()
+    assert m.check_residues(p, h)
+    h[70000] = p
+    assert not m.check_residues(p, h)
+    with pytest.raises(m.MontError) as e:
+        m.check_residues(4, h)
+    assert e.value.code == m.MONT_EINVAL
