@@ -34,7 +34,7 @@ enum {
     MONT_OK = 0,
     MONT_EINVAL = -1,      /* bad argument (modulus, pointer, size, overlap, flags)   */
     MONT_ENOMEM = -2,      /* device or host allocation failed                         */
-    MONT_ERANGE = -3,      /* size beyond what the modulus / plan supports             */
+    MONT_ERANGE = -3,      /* size (or, for mont_check_residues, a value) out of range */
     MONT_ETIMEOUT = -4,    /* a bounded device-side wait gave up                       */
     MONT_ECUDA = -5,       /* a CUDA runtime call or kernel launch failed              */
     MONT_EUNSUPPORTED = -6 /* valid request this build does not implement              */

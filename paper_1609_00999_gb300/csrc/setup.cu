@@ -1,4 +1,5 @@
 // setup.cu -- host-side Montgomery set-up (Sec. 3.1), error strings, device info.
+#include <atomic>
 #include <cstdio>
 
 #include "common.cuh"
@@ -49,17 +50,20 @@ int check_ctx(const mont_ctx *ctx)
     return MONT_OK;
 }
 
+// Calls may come from several host threads at once (the server's launcher
+// threads, callers on different streams): the cache entries are atomics,
+// and a race only makes two threads store the same count.
 int device_sm_count()
 {
-    static int cache[128];
+    static std::atomic<int> cache[128];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return 0;
-    if (cache[dev] == 0) {
-        int n = 0;
+    int n = cache[dev].load(std::memory_order_relaxed);
+    if (n == 0) {
         if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-        cache[dev] = n;
+        cache[dev].store(n, std::memory_order_relaxed);
     }
-    return cache[dev];
+    return n;
 }
 
 }  // namespace mont
@@ -81,7 +85,7 @@ extern "C" const char *mont_strerror(int code)
     case MONT_OK: return "success";
     case MONT_EINVAL: return "invalid argument";
     case MONT_ENOMEM: return "out of memory";
-    case MONT_ERANGE: return "size out of range for this modulus or plan";
+    case MONT_ERANGE: return "value or size out of range for this modulus or plan";
     case MONT_ETIMEOUT: return "bounded device wait timed out";
     case MONT_ECUDA: return "CUDA runtime error";
     case MONT_EUNSUPPORTED: return "unsupported request";
