@@ -276,7 +276,10 @@ int polymul_batch_plan_get_config(const polymul_batch_plan *plan, polymul_batch_
 int polymul_batch_plan_set_config(polymul_batch_plan *plan, const polymul_batch_config *cfg);
 
 /* Queue the whole batch on `stream`: one memset of the counters and one
- * persistent kernel launch.  The operands must be ready when it runs. */
+ * persistent kernel launch.  The operands must be ready when it runs.  Runs
+ * of one plan share its counters and scratch: two of them must not be in
+ * flight at once (queue them on one stream, or order them with events);
+ * distinct plans are independent. */
 int polymul_batch_run(polymul_batch_plan *plan, cudaStream_t stream);
 
 /* Same work replayed from a CUDA graph captured on first use (re-captured

@@ -617,6 +617,8 @@ int batch_build(const polymul_desc *descs, size_t count, BatchHost &out, std::ve
         }
         for (; si < sm.size(); si++) jobs.push_back(sm[si]);
     }
+    for (const std::vector<Job> &jobs : out.jobs)
+        if (jobs.size() > UINT32_MAX) return MONT_ERANGE;   // the kernel counts jobs in 32 bits
     return MONT_OK;
 }
 
