@@ -400,6 +400,8 @@ def polymul_many_ws(p, a, b, workspace, out=None, stream=None):
     lc = la + lb - 1
     if out is None:
         out = torch.empty((count, lc), dtype=a.dtype, device=a.device)
+    elif out.numel() != count * lc:
+        raise ValueError("out must have %d elements" % (count * lc))
     ws_ptr = workspace.data_ptr() if workspace is not None else None
     ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
     _check(lib().polymul_many_ws(int(p), _dev_ptr(a, "a"), la, _dev_ptr(b, "b"), lb, _dev_ptr(out, "out"), count,
@@ -426,6 +428,28 @@ def polymul_noalloc(plan, a, b, out=None, stream=None):
     return out
 
 
+def _check_packed_bounds(na, a_off, la, nb, b_off, lb, nc, c_off):
+    """ValueError unless, for every product i, a[a_off[i]:][:la[i]],
+    b[b_off[i]:][:lb[i]] and c[c_off[i]:][:la[i] + lb[i] - 1] lie inside
+    tensors of na, nb and nc words (lengths >= 1, offsets >= 0)."""
+    import numpy as np
+    cols = [np.asarray(x, dtype=np.int64).reshape(-1) for x in (a_off, la, b_off, lb, c_off)]
+    if len({x.size for x in cols}) != 1:
+        raise ValueError("offset and length sequences differ in size")
+    ao, la_, bo, lb_, co = cols
+    if ao.size == 0:
+        return
+    if (la_ < 1).any() or (lb_ < 1).any():
+        raise ValueError("product lengths must be >= 1")
+    if (ao < 0).any() or (bo < 0).any() or (co < 0).any():
+        raise ValueError("offsets must be >= 0")
+    for name, end, n in (("a", ao + la_, na), ("b", bo + lb_, nb), ("c", co + la_ + lb_ - 1, nc)):
+        bad = np.flatnonzero(end > n)
+        if bad.size:
+            raise ValueError("product %d: %s slice ends at %d, beyond the %d-word tensor"
+                             % (bad[0], name, end[bad[0]], n))
+
+
 class PolymulBatchPlan:
     """Owner of a ``polymul_batch_plan *``: an uneven batch of products run by
     one persistent kernel launch (or a CUDA graph replay of it)."""
@@ -443,7 +467,9 @@ class PolymulBatchPlan:
     @classmethod
     def from_packed(cls, primes, a, a_off, la, b, b_off, lb, c, c_off):
         """Products packed back to back: product i uses a[a_off[i]:][:la[i]] etc.
-        (a, b, c int32/uint32 CUDA tensors; offsets and lengths host sequences)."""
+        (a, b, c int32/uint32 CUDA tensors; offsets and lengths host sequences).
+        Every slice must lie inside its tensor: the kernel sees raw addresses."""
+        _check_packed_bounds(a.numel(), a_off, la, b.numel(), b_off, lb, c.numel(), c_off)
         pa, pb, pc = _dev_ptr(a, "a"), _dev_ptr(b, "b"), _dev_ptr(c, "c")
         descs = [PolymulDesc(pa + 4 * int(ao), pb + 4 * int(bo), pc + 4 * int(co), int(x), int(y), int(p), 0)
                  for p, ao, x, bo, y, co in zip(primes, a_off, la, b_off, lb, c_off)]
@@ -529,6 +555,19 @@ def completion_dtype():
     return np.dtype([("id", np.uint64), ("status", np.int32), ("reserved", np.int32)])
 
 
+def _check_request_array(reqs, start, stop):
+    """The library reads mont_request structs straight from the array's
+    memory: it must be a C-contiguous 1-D array of request_dtype() and
+    0 <= start <= stop <= len(reqs)."""
+    import numpy as np
+    if not isinstance(reqs, np.ndarray) or reqs.dtype != request_dtype():
+        raise TypeError("reqs must be a numpy array of request_dtype()")
+    if reqs.ndim != 1 or not reqs.flags.c_contiguous:
+        raise ValueError("reqs must be a 1-D C-contiguous array")
+    if not (0 <= start <= stop <= len(reqs)):
+        raise ValueError("need 0 <= start <= stop <= len(reqs), got %r, %r" % (start, stop))
+
+
 class MontServer:
     """Owner of a ``mont_server *`` (continuous-batching request server)."""
 
@@ -544,6 +583,7 @@ class MontServer:
     def submit(self, reqs, start=0, stop=None):
         """Queue requests [start, stop) of a request_dtype() array."""
         stop = len(reqs) if stop is None else stop
+        _check_request_array(reqs, start, stop)
         if stop > start:
             ptr = reqs.ctypes.data + start * reqs.dtype.itemsize
             _check(lib().mont_server_submit(self._h, ptr, stop - start), "mont_server_submit")
