@@ -115,6 +115,34 @@ def test_alone_equals_in_the_mix(m):
         assert np.array_equal(got[co:co + la + lb - 1], alone), i
 
 
+def check_uneven_sampled(wl, got, stride=25, largest=10):
+    """Every stride-th product and the `largest` longest ones equal the
+    oracle's product; every word of every result is a residue of its
+    product's prime (the buffer was filled with 0xFFFFFFFF, so this also shows
+    that every word was written)."""
+    lc = (wl.la + wl.lb - 1).astype(np.int64)
+    idx = np.union1d(np.arange(0, len(wl), stride), np.argsort(lc, kind="stable")[-largest:])
+    for i in idx:
+        ao, la, bo, lb, co = (int(wl.a_off[i]), int(wl.la[i]), int(wl.b_off[i]), int(wl.lb[i]), int(wl.c_off[i]))
+        ref = oracle.polymul_ntt(int(wl.primes[i]), wl.a[ao:ao + la], wl.b[bo:bo + lb])
+        assert np.array_equal(got[co:co + la + lb - 1], ref), i
+    for p in np.unique(wl.primes):
+        mask = np.repeat(wl.primes == p, lc)
+        assert (got[mask] < p).all(), int(p)
+    return len(idx)
+
+
+def test_uneven_full_size_sampled(m):
+    """The whole 10,000-product uneven workload (L log-uniform in [2^6, 2^16],
+    primes uniform from the three Fourier primes), tuned and replayed from a
+    CUDA graph as the benchmark runs it, twice over the same buffers."""
+    wl = synth.batch_uneven()
+    plan, _, _, dc = run_packed(m, wl, graph=True, tune=True)
+    plan.run_graph()
+    assert plan.status() == m.MONT_OK
+    assert check_uneven_sampled(wl, to_host(dc)[:wl.c_size]) >= 400
+
+
 def test_uneven_config_sample(m):
     """A 600-product slice of the 10,000-product uneven workload (L log-uniform in [2^6, 2^16])."""
     wl_full = synth.batch_uneven(count=600)

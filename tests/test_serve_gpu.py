@@ -32,9 +32,20 @@ def stream_case(n=400, lo=1 << 8, hi=1 << 15, rate=20000.0, seed=700):
     return wl, arrivals
 
 
-def test_stream_results_equal_alone(m):
+STREAMS = {
+    # lengths up to 2^15 under a 24 MiB budget: admission waits, many small batches
+    "small": dict(case=dict(n=400, hi=1 << 15, rate=20000.0), max_log2n=16, budget=24 << 20, cap=1 << 17),
+    # the serving workload's full length range, L up to 2^20 (N up to 2^21)
+    "full_range": dict(case=dict(n=160, hi=1 << 20, rate=2000.0, seed=701), max_log2n=21, budget=256 << 20,
+                       cap=1 << 22),
+}
+
+
+@pytest.mark.parametrize("name", sorted(STREAMS))
+def test_stream_results_equal_alone(m, name):
     import torch
-    wl, arrivals = stream_case()
+    cfg = STREAMS[name]
+    wl, arrivals = stream_case(**cfg["case"])
     da, db = to_dev(wl.a), to_dev(wl.b)
     host_a = torch.from_numpy(wl.a.view(np.int32)).pin_memory()       # half the requests read host memory
     hc = torch.full((wl.c_size,), -1, dtype=torch.int32).pin_memory()
@@ -44,8 +55,8 @@ def test_stream_results_equal_alone(m):
     reqs = serve.make_requests(wl.primes, wl.la, wl.lb, a_ptrs,
                                db.data_ptr() + 4 * wl.b_off.astype(np.int64),
                                hc.data_ptr() + 4 * wl.c_off.astype(np.int64))
-    budget = 24 << 20                                                # forces admission waits
-    server = m.MontServer(synth.PRIMES, 16, budget, slots=3, max_batch_coeffs=1 << 17)
+    budget = cfg["budget"]
+    server = m.MontServer(synth.PRIMES, cfg["max_log2n"], budget, slots=3, max_batch_coeffs=cfg["cap"])
     lat, status, makespan = serve.run_stream(server, reqs, arrivals)
     st = server.stats()
     server.close()
