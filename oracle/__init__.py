@@ -32,7 +32,9 @@ _lib = None
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
+        # ORACLE_LIB: load another build of oracle.c instead (the mutation
+        # test loads copies with planted mistakes to show the pins catch them).
+        path = os.environ.get("ORACLE_LIB") or _build.build()
         L = ctypes.CDLL(path)
         L.or_setup.argtypes = [ctypes.c_uint32, ctypes.POINTER(OrCtx)]
         L.or_setup.restype = ctypes.c_int

@@ -115,6 +115,19 @@ def test_mont_mul_brute_force_all_pairs(p):
         assert zz == _redc_alg2(x, y, p, c.p_prime)
 
 
+@pytest.mark.parametrize("p", [q for q in TINY_ODD if q < 100])
+def test_mont_fma_brute_force_all_triples(p):
+    """For every x, y, z the result w lies in [0, P) and w R == x y + z R
+    (mod P): REDC of x y (Alg. 2) followed by a modular add of z, which
+    Sec. 3.1 notes is the same in Montgomery form.  Checked on w itself,
+    not through from_mont, which would hide a missing final reduction."""
+    g = np.arange(p, dtype=np.int64)
+    xs, ys, zs = (v.ravel() for v in np.meshgrid(g, g, g, indexing="ij"))
+    w = oracle.mont_fma(p, xs, ys, zs).astype(np.int64)
+    assert np.all((w >= 0) & (w < p))
+    assert np.all((w * (R % p) - xs * ys - zs * (R % p)) % p == 0)
+
+
 @pytest.mark.parametrize("p", TINY_ODD)
 def test_to_from_mont_brute_force(p):
     x = np.arange(p, dtype=np.uint32)
@@ -154,6 +167,12 @@ def test_adversarial_values(p):
     got = oracle.mont_mul(p, xs, ys)
     for a, b, r in zip(xs.tolist(), ys.tolist(), got.tolist()):
         assert r == _redc_alg2(a, b, p, c.p_prime)
+    # mont_fma at the same values, with every z: sums past P must wrap
+    xs3, zs3 = np.repeat(xs, vals.size), np.tile(vals, xs.size)
+    ys3 = np.repeat(ys, vals.size)
+    fma = oracle.mont_fma(p, xs3, ys3, zs3)
+    for a, b, z, w in zip(xs3.tolist(), ys3.tolist(), zs3.tolist(), fma.tolist()):
+        assert w < p and (w * R - a * b - z * R) % p == 0
 
 
 def test_golden_examples():
