@@ -34,7 +34,7 @@ def test_mont_setup_matches_oracle(L, p):
     assert (ctx.p, ctx.p_prime, ctx.r_mod_p, ctx.r2_mod_p) == (ref.p, ref.p_prime, ref.r_mod_p, ref.r2_mod_p)
 
 
-@pytest.mark.parametrize("p", [0, 1, 2, 4, 2 ** 31, 2 ** 32 - 1])
+@pytest.mark.parametrize("p", [0, 1, 2, 4, 2 ** 31, 2 ** 31 + 1, 3 * 2 ** 30 + 1, 2 ** 32 - 1])
 def test_mont_setup_rejects(L, p):
     import paper_1609_00999_gb300 as m
     with pytest.raises(m.MontError) as e:

@@ -55,6 +55,13 @@ MUTANTS = [
     ("polymul_ntt_size_one_short", "while (n < lc) n <<= 1;", "while (n + 1 < lc) n <<= 1;"),
     ("polymul_ntt_squares_a", "fa[k] = or_mulmod(fa[k], fb[k], p);", "fa[k] = or_mulmod(fa[k], fa[k], p);"),
     ("polymul_batch_b_at_a_offset", "b + b_off[i]", "b + a_off[i]"),
+    ("primitive_root_trial_bound", "(uint64_t)q * q <= m", "(uint64_t)q * q < m"),
+    ("ninv_of_n_plus_1", "or_invmod(n % p, p)", "or_invmod((n + 1) % p, p)"),
+    ("setup_accepts_odd_above_2_31", "p >= 0x80000000u) return -1;", "p == 0xFFFFFFFFu) return -1;"),
+    ("invmod_negative_kept", "if (old_s < 0) old_s += (int64_t)m;", "(void)0;"),
+    ("schoolbook_no_accumulate", "c[i + j] = (uint32_t)(((uint64_t)c[i + j] + or_mulmod(a[i], b[j], p)) % p);",
+     "c[i + j] = or_mulmod(a[i], b[j], p);"),
+    ("mulmod_vec_squares_x", "out[i] = or_mulmod(x[i], y[i], p);", "out[i] = or_mulmod(x[i], x[i], p);"),
 ]
 
 

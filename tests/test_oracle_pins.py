@@ -217,6 +217,36 @@ def test_primitive_root_and_fermat(row):
     assert oracle.powmod(g, p - 1, p) == 1
 
 
+def _small_primes(limit):
+    sieve = bytearray([1]) * limit
+    sieve[:2] = b"\x00\x00"
+    for i in range(2, int(limit ** 0.5) + 1):
+        if sieve[i]:
+            sieve[i * i::i] = bytearray(len(sieve[i * i::i]))
+    return [i for i in range(3, limit) if sieve[i]]
+
+
+def test_primitive_root_brute_force_small_primes():
+    """The smallest primitive root of every odd prime below 5000 is the
+    smallest g whose powers g, g^2, ... first return to 1 at exponent P - 1
+    (order found by repeated multiplication, no factorisation).  The range
+    includes 3631, 4051 and 4733, where P - 1 leaves the square of a prime
+    after trial division by the smaller factors and a candidate below the
+    true root has order (P - 1) / q: a factoring step that stops one trial
+    divisor early accepts it."""
+    for p in _small_primes(5000):
+        g = 2
+        while True:
+            x, order = g, 1
+            while x != 1:
+                x = x * g % p
+                order += 1
+            if order == p - 1:
+                break
+            g += 1
+        assert oracle.primitive_root(p) == g, p
+
+
 @pytest.mark.parametrize("p", synth.PRIMES)
 def test_roots_of_unity_have_exact_order(p):
     two_adic = ((p - 1) & -(p - 1)).bit_length() - 1
