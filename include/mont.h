@@ -109,7 +109,7 @@ int fourier_redc_mul(const mont_ctx *ctx, const uint32_t *a, const uint32_t *b, 
  * n == 0), MONT_ERANGE if some word is >= p, MONT_EINVAL for p even, p < 3,
  * p >= 2^31, or x NULL with n > 0.  One read of x (4 B per element).
  * Unlike every other call it is SYNCHRONOUS: it runs on `stream` after the
- * work queued there, reads the verdict back and returns once the stream has
+ * work queued there, reads its result back and returns once the stream has
  * drained.  A debugging aid for callers whose data did not come from this
  * library; the product calls never run it.
  */

@@ -55,7 +55,7 @@ extern "C" int mont_check_residues(uint32_t p, const uint32_t *x, size_t n, cuda
         cudaGetLastError();
         return MONT_ENOMEM;
     }
-    uint32_t verdict = 0;
+    uint32_t flagged = 0;
     int rc = cudaMemsetAsync(bad, 0, sizeof(uint32_t), stream) == cudaSuccess ? MONT_OK : MONT_ECUDA;
     if (rc == MONT_OK) {
         if (vec) mont::k_check_residues<true><<<grid, kCheckThreads, 0, stream>>>(x, n, p, bad);
@@ -63,10 +63,10 @@ extern "C" int mont_check_residues(uint32_t p, const uint32_t *x, size_t n, cuda
         rc = mont::launch_status();
     }
     if (rc == MONT_OK &&
-        cudaMemcpyAsync(&verdict, bad, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+        cudaMemcpyAsync(&flagged, bad, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream) != cudaSuccess)
         rc = MONT_ECUDA;
     if (cudaFreeAsync(bad, stream) != cudaSuccess) rc = MONT_ECUDA;
     if (cudaStreamSynchronize(stream) != cudaSuccess) rc = MONT_ECUDA;
     if (rc != MONT_OK) return rc;
-    return verdict ? MONT_ERANGE : MONT_OK;
+    return flagged ? MONT_ERANGE : MONT_OK;
 }
