@@ -175,6 +175,25 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def run_section(extra, errors, key, fn):
+    """Runs one secondary section into extra[key].  A failure (a parity spot
+    check, a device error) is recorded in errors[key] and its traceback
+    printed to stderr, so the headline measurement is still reported."""
+    try:
+        extra[key] = fn()
+    except Exception as e:  # noqa: BLE001 -- any failure of a section is reported, not raised
+        import traceback
+        traceback.print_exc(file=sys.stderr)
+        errors[key] = "%s: %s" % (type(e).__name__, str(e)[:300])
+        try:
+            import torch
+            if torch.cuda.is_available():
+                torch.cuda.synchronize()
+                torch.cuda.empty_cache()
+        except Exception:  # noqa: BLE001 -- a broken context shows in the next section's error
+            pass
+
+
 def cpu_oracle_step(arrays, n_sample):
     """Oracle mont_mul + mont_fma over the first n_sample elements of each prime's operands."""
     import oracle
@@ -347,28 +366,28 @@ def run_gpu(args, ws, rank, local):
         cpu = {"value": 3 * 2 * n / t / 1e9, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                "sample": "one full step: 2^%d residues x 3 primes x {mont_mul, mont_fma}" % args.log2n}
 
-    extra = {}
+    extra, errors = {}, {}
     if rank == 0 and ws == 1:
         import bench_polymul as bp
         peaks = {"hbm_gbs": measured_peaks()[0], "sm_max_mhz": measured_sm_max_mhz()}
         secs = [x for x in args.sections.split(",") if x]
         sampler2 = ClockSampler(bus)
         sampler2.start()
-        if "roundtrip" in secs:
-            extra["roundtrip_65536"] = bp.roundtrip_small(m, torch)
-        if "ntt" in secs:
-            extra["ntt_fwd_inv"] = bp.ntt_transforms(m, torch, peaks)
-        if "uniform" in secs:
-            extra["polymul_uniform_4096x2048"] = bp.uniform_batch(m, torch, peaks, cpu=not args.no_cpu_baseline)
-        if "reductions" in secs:
-            extra["reductions_elementwise_2e28"] = bp.reductions_elementwise(m, torch, peaks)
-            extra["polymul_alg2_vs_alg3_4096x2048"] = bp.reduction_ab(m, torch)
-        if "uneven" in secs:
-            cfg = tuple(int(x) for x in args.batch_config.split(",")) if args.batch_config else None
-            extra["polymul_uneven_10000"] = bp.uneven_batch(m, torch, peaks, cpu=not args.no_cpu_baseline,
-                                                            per_product=not args.no_per_product, config=cfg)
-        if "serve" in secs:
-            extra["serve_50000"] = bp.serve_stream(m, torch)
+        cpu_on = not args.no_cpu_baseline
+        cfg = tuple(int(x) for x in args.batch_config.split(",")) if args.batch_config else None
+        sections = [
+            ("roundtrip", "roundtrip_65536", lambda: bp.roundtrip_small(m, torch)),
+            ("ntt", "ntt_fwd_inv", lambda: bp.ntt_transforms(m, torch, peaks)),
+            ("uniform", "polymul_uniform_4096x2048", lambda: bp.uniform_batch(m, torch, peaks, cpu=cpu_on)),
+            ("reductions", "reductions_elementwise_2e28", lambda: bp.reductions_elementwise(m, torch, peaks)),
+            ("reductions", "polymul_alg2_vs_alg3_4096x2048", lambda: bp.reduction_ab(m, torch)),
+            ("uneven", "polymul_uneven_10000",
+             lambda: bp.uneven_batch(m, torch, peaks, cpu=cpu_on, per_product=not args.no_per_product, config=cfg)),
+            ("serve", "serve_50000", lambda: bp.serve_stream(m, torch)),
+        ]
+        for name, key, fn in sections:
+            if name in secs:
+                run_section(extra, errors, key, fn)
         if secs:
             extra["clocks_polymul_sections"] = sampler2.stop()
         else:
@@ -385,6 +404,8 @@ def run_gpu(args, ws, rank, local):
                 "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
                 "cpu_baseline": cpu}
         line.update(extra)
+        if errors:
+            line["section_errors"] = errors
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -72,3 +72,20 @@ def test_batch_hbm_bytes_pass_structure():
     sizes = [1 << int(2 * L - 2).bit_length() for L in lens]
     vals = [bp.batch_hbm_bytes(s, int(L), int(L)) for s, L in zip(sizes, lens)]
     assert vals == sorted(vals)
+
+
+def test_section_failure_is_recorded_not_raised(capsys):
+    """A failing secondary section leaves the others and the headline line
+    intact and is reported under its key."""
+    import bench
+    extra, errors = {}, {}
+    bench.run_section(extra, errors, "first", lambda: {"value": 1.0})
+
+    def broken():
+        raise AssertionError("batch parity spot check failed")
+
+    bench.run_section(extra, errors, "second", broken)
+    bench.run_section(extra, errors, "third", lambda: {"value": 3.0})
+    assert extra == {"first": {"value": 1.0}, "third": {"value": 3.0}}
+    assert errors == {"second": "AssertionError: batch parity spot check failed"}
+    assert "batch parity spot check failed" in capsys.readouterr().err
