@@ -139,6 +139,11 @@ typedef struct ntt_plan ntt_plan;
  * call during stream capture).  MONT_EINVAL for a bad prime or NULL out,
  * MONT_ERANGE for an unsupported size, MONT_ENOMEM / MONT_ECUDA on failure. */
 int ntt_plan_create(uint32_t p, uint32_t log2n, ntt_plan **out);
+
+/* Frees the plan object (NULL is a no-op).  Its twiddle tables stay cached
+ * in device memory for later plans and products of the same (device, p) and
+ * are released with the process; work already queued with the plan may
+ * still run. */
 void ntt_plan_destroy(ntt_plan *plan);
 
 /* In-place forward transform of `batch` contiguous rows of N residues
