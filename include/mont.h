@@ -302,6 +302,31 @@ int polymul_batch_status(polymul_batch_plan *plan, cudaStream_t stream);
  * Returns the status of the last run. */
 int polymul_batch_plan_tune(polymul_batch_plan *plan, cudaStream_t stream, int trials);
 
+/* One-shot batch without a plan: the same persistent kernel and results as
+ * polymul_batch_plan_create + polymul_batch_run, in a fixed launch shape
+ * (the 3-CTA/SM register budget, job order 0), with every device table of
+ * the batch in the caller's workspace.  Each call validates the
+ * descriptors, builds the job list on the host, queues copies of it and of
+ * the product table from pageable host memory into the workspace (so not
+ * during stream capture; a plan can be captured), and launches the kernel.
+ * workspace: device memory, 256-byte aligned (as cudaMalloc returns), at
+ * least polymul_batch_workspace_bytes(descs, count) bytes; it must not be
+ * used by other work until the queued kernel finishes (calls on one stream
+ * may share it).  Descriptor errors as polymul_batch_plan_create;
+ * MONT_EINVAL for a missing, misaligned or short workspace.  The twiddle
+ * tables of each prime are built on first use (make the first call outside
+ * stream capture).  count == 0 is a no-op. */
+int polymul_batch(const polymul_desc *descs, size_t count, void *workspace, size_t ws_bytes, cudaStream_t stream);
+
+/* Host only: workspace bytes polymul_batch needs for these descriptors
+ * (counters, product table, job list and 2N words of scratch per product
+ * with N > 2^13); 0 for count == 0 or invalid descriptors. */
+size_t polymul_batch_workspace_bytes(const polymul_desc *descs, size_t count);
+
+/* Synchronises `stream`, then reports MONT_OK, or MONT_ETIMEOUT when a
+ * bounded wait inside the last polymul_batch run on this workspace expired. */
+int polymul_batch_check(const void *workspace, cudaStream_t stream);
+
 /* Bound of every device-side wait of the plan (default 2^22 polls, 2 s). */
 int polymul_batch_plan_set_wait_limit(polymul_batch_plan *plan, uint32_t iterations, uint64_t nanoseconds);
 

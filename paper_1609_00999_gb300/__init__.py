@@ -12,6 +12,7 @@ from ._binding import (MONT_ECUDA, MONT_EINVAL, MONT_ENOMEM, MONT_ERANGE, MONT_E
 from ._binding import mont_release_workspaces, polymul_many_ws, polymul_noalloc, polymul_workspace_bytes  # noqa: F401
 from ._binding import polymul_many_fourier  # noqa: F401
 from ._binding import (PolymulBatchConfig, PolymulBatchPlan, PolymulDesc,  # noqa: F401
-                       polymul_batch_describe, polymul_batch_plan_create)
+                       polymul_batch, polymul_batch_check, polymul_batch_describe, polymul_batch_plan_create,
+                       polymul_batch_workspace_bytes)
 from ._binding import MontServer, MontServerStats, completion_dtype, request_dtype  # noqa: F401
 from ._binding import barrett_mulmod, check_residues, fourier_redc_mul  # noqa: F401

@@ -136,6 +136,12 @@ def _declare_batch(L):
     L.polymul_batch_plan_tune.argtypes = [_vp, _vp, ctypes.c_int]
     L.polymul_batch_plan_set_wait_limit.argtypes = [_vp, ctypes.c_uint32, ctypes.c_uint64]
     L.polymul_batch_plan_inject_stall.argtypes = [_vp]
+    L.polymul_batch.argtypes = [ctypes.POINTER(PolymulDesc), _sz, _vp, _sz, _vp]
+    L.polymul_batch.restype = ctypes.c_int
+    L.polymul_batch_workspace_bytes.argtypes = [ctypes.POINTER(PolymulDesc), _sz]
+    L.polymul_batch_workspace_bytes.restype = _sz
+    L.polymul_batch_check.argtypes = [_vp, _vp]
+    L.polymul_batch_check.restype = ctypes.c_int
     for name in ("polymul_batch_plan_create", "polymul_batch_plan_get_config", "polymul_batch_plan_set_config",
                  "polymul_batch_run", "polymul_batch_run_graph", "polymul_batch_status", "polymul_batch_plan_tune",
                  "polymul_batch_plan_set_wait_limit", "polymul_batch_plan_inject_stall"):
@@ -541,6 +547,37 @@ def polymul_batch_describe(descs, order):
     _check(lib().polymul_batch_describe(arr, len(descs), int(order), jobs.ctypes.data, n.value, prods.ctypes.data,
                                         ctypes.byref(n)), "polymul_batch_describe")
     return jobs[:n.value], prods[:len(descs)]
+
+
+def _desc_array(descs):
+    arr = (PolymulDesc * max(1, len(descs)))()
+    for i, d in enumerate(descs):
+        arr[i] = d
+    return arr
+
+
+def polymul_batch_workspace_bytes(descs):
+    """Workspace bytes polymul_batch needs for these descriptors (host only;
+    0 for an empty list or invalid descriptors)."""
+    return int(lib().polymul_batch_workspace_bytes(_desc_array(descs), len(descs)))
+
+
+def polymul_batch(descs, workspace, stream=None):
+    """One-shot uneven batch: PolymulDesc list, caller-owned CUDA workspace
+    tensor (any dtype, contiguous) of at least polymul_batch_workspace_bytes
+    bytes.  Queues the work and returns; polymul_batch_check reports waits
+    that expired."""
+    if not isinstance(workspace, torch.Tensor) or not workspace.is_cuda or not workspace.is_contiguous():
+        raise ValueError("workspace must be a contiguous CUDA tensor")
+    nbytes = workspace.numel() * workspace.element_size()
+    _check(lib().polymul_batch(_desc_array(descs), len(descs), workspace.data_ptr(), nbytes,
+                               _stream_handle(stream, workspace.device)), "polymul_batch")
+
+
+def polymul_batch_check(workspace, stream=None):
+    """Synchronises the stream; MONT_OK or MONT_ETIMEOUT for the last
+    polymul_batch run on this workspace."""
+    return int(lib().polymul_batch_check(workspace.data_ptr(), _stream_handle(stream, workspace.device)))
 
 
 # numpy mirrors of mont_request / mont_completion (48 and 16 bytes)

@@ -72,3 +72,31 @@ def test_no_cpu_fallback_when_library_missing(monkeypatch, tmp_path):
     monkeypatch.setattr(b, "_lib", None)
     with pytest.raises(RuntimeError):
         b.lib()
+
+
+def test_one_shot_batch_host_checks(L):
+    """polymul_batch sizes its workspace and rejects bad arguments on the
+    host, before any device work (descriptor addresses are not touched)."""
+    import paper_1609_00999_gb300 as m
+    a0, c0 = 0x100000, 0x40000000
+
+    def desc(la, lb, k):
+        return m.PolymulDesc(a0 + k * 0x1000000, a0 + k * 0x1000000 + 0x800000, c0 + k * 0x1000000, la, lb,
+                             synth.P1, 0)
+
+    descs = [desc(100, 50, 0), desc(20000, 20000, 1), desc(3, 1, 2)]
+    need = m.polymul_batch_workspace_bytes(descs)
+    assert need >= 2 * (1 << 16) * 4                     # the N = 2^16 product's scratch
+    assert m.polymul_batch_workspace_bytes(descs[:1]) < need
+    assert m.polymul_batch_workspace_bytes([]) == 0
+    assert m.polymul_batch_workspace_bytes([desc(0, 5, 0)]) == 0
+    arr = (m.PolymulDesc * 3)(*descs)
+    ws = ctypes.c_void_p(0x7f0000000000)
+    assert L.polymul_batch(arr, 3, None, need, None) == m.MONT_EINVAL
+    assert L.polymul_batch(arr, 3, ws, need - 1, None) == m.MONT_EINVAL
+    assert L.polymul_batch(arr, 3, ctypes.c_void_p(0x7f0000000010), need, None) == m.MONT_EINVAL
+    assert L.polymul_batch(None, 3, ws, need, None) == m.MONT_EINVAL
+    assert L.polymul_batch(None, 0, None, 0, None) == m.MONT_OK
+    bad = (m.PolymulDesc * 1)(desc(5, 0, 0))
+    assert L.polymul_batch(bad, 1, ws, need, None) == m.MONT_EINVAL
+    assert L.polymul_batch_check(None, None) == m.MONT_EINVAL

@@ -115,6 +115,32 @@ def test_alone_equals_in_the_mix(m):
         assert np.array_equal(got[co:co + la + lb - 1], alone), i
 
 
+def one_shot(m, wl, ws=None):
+    import torch
+    da, db = to_dev(wl.a), to_dev(wl.b)
+    dc = torch.full((max(1, wl.c_size),), -1, dtype=torch.int32, device="cuda")
+    descs = [m.PolymulDesc(da.data_ptr() + 4 * int(wl.a_off[i]), db.data_ptr() + 4 * int(wl.b_off[i]),
+                           dc.data_ptr() + 4 * int(wl.c_off[i]), int(wl.la[i]), int(wl.lb[i]), int(wl.primes[i]), 0)
+             for i in range(len(wl))]
+    need = m.polymul_batch_workspace_bytes(descs)
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(max(1, need), dtype=torch.uint8, device="cuda")
+    m.polymul_batch(descs, ws)
+    assert m.polymul_batch_check(ws) == m.MONT_OK
+    return to_host(dc)[:wl.c_size], ws
+
+
+def test_one_shot_batch_matches_oracle(m):
+    """polymul_batch (no plan, tables in the caller's workspace) on every
+    size 2^0 .. 2^21, then a second batch reusing the same workspace."""
+    wl = mixed_batch()
+    got, ws = one_shot(m, wl)
+    assert np.array_equal(got, oracle_packed(wl))
+    wl2 = synth.batch_uneven(count=300, hi=1 << 15)
+    got2, _ = one_shot(m, wl2, ws)
+    assert np.array_equal(got2, oracle_packed(wl2))
+
+
 def check_uneven_sampled(wl, got, stride=25, largest=10):
     """Every stride-th product and the `largest` longest ones equal the
     oracle's product; every word of every result is a residue of its
