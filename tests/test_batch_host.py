@@ -94,6 +94,22 @@ def test_mixed_sizes_job_lists(m, order):
     assert {int(p[0]) for p in prods} >= set(range(0, 22))
 
 
+@pytest.mark.parametrize("order", [0, 1, 2, 3])
+def test_random_batches_job_lists(m, order):
+    """40 seeded random batches of 1 to 300 products, lengths log-uniform in
+    [1, 2^20] and drawn separately for a and b: many with only a few split
+    products, fewer than the pipelined orders' lag of 32 or 64."""
+    import numpy as np
+    rng = np.random.default_rng(8800 + order)
+    for trial in range(40):
+        count = int(rng.integers(1, 301))
+        la = np.exp(rng.uniform(0, np.log(1 << 20), count)).astype(np.int64).clip(1, 1 << 20)
+        lb = np.exp(rng.uniform(0, np.log(1 << 20), count)).astype(np.int64).clip(1, 1 << 20)
+        primes = [synth.PRIMES[i] for i in rng.integers(0, 3, count)]
+        jobs, prods = m.polymul_batch_describe(fake_descs(m, la, lb, primes), order)
+        check_job_list(jobs, prods)
+
+
 def test_describe_rejects_bad_input(m):
     d = fake_descs(m, [10], [10], [synth.P1])
     with pytest.raises(m.MontError):
