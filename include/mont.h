@@ -173,7 +173,9 @@ int polymul(uint32_t p, const uint32_t *a, size_t la, const uint32_t *b, size_t 
  * product; polymul and polymul_many take it from a library-owned buffer per
  * (device, stream), at most 1 GiB (larger batches run in chunks), allocated
  * or grown with cudaMalloc on first need: size it outside stream capture.
- * Concurrent calls on different streams use different buffers. */
+ * Concurrent calls on different streams use different buffers; calls that
+ * share a stream must come from one host thread at a time (a call that
+ * grows the buffer frees the one another call is about to use). */
 int polymul_many(uint32_t p, const uint32_t *a, size_t la, const uint32_t *b, size_t lb, uint32_t *c,
                  size_t count, cudaStream_t stream);
 
