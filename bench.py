@@ -18,7 +18,6 @@ same workload per step (there is no reference implementation to install:
 the paper publishes no code).
 """
 import argparse
-import hashlib
 import json
 import os
 import statistics
@@ -41,7 +40,6 @@ METRIC = "Gmulmod/s (elementwise mont_mul + mont_fma)"
 UNIT = "Gmulmod/s"
 WORKLOAD = ("elementwise mont_mul + mont_fma over 2^28 uint32 residues per operand, uniform in [0,P), "
             "P in {2013265921, 469762049, 754974721}")
-KERNEL_SOURCES = ("paper_1609_00999_gb300/csrc/elementwise.cu", "paper_1609_00999_gb300/csrc/mont_arith.cuh")
 
 
 def parse_args():
@@ -55,9 +53,11 @@ def parse_args():
     ap.add_argument("--log2n", type=int, default=28, help="elements per operand (default 2^28)")
     ap.add_argument("--batch-config", default=None,
                     help="uneven section: fixed launch shape CTAS_PER_SM,ORDER,KERNEL instead of autotuning")
-    ap.add_argument("--sections", default="roundtrip,ntt,uniform,reductions,uneven,serve",
-                    help="extra sections to run (comma list of roundtrip, ntt, uniform, reductions, uneven, "
+    ap.add_argument("--sections", default="probe,roundtrip,ntt,uniform,reductions,uneven,serve",
+                    help="extra sections to run (comma list of probe, roundtrip, ntt, uniform, reductions, uneven, "
                          "serve; empty for none)")
+    ap.add_argument("--no-sections-all-ranks", dest="sections_all_ranks", action="store_false",
+                    help="with more than one rank, skip the extra sections (default: every rank runs them)")
     ap.add_argument("--no-per-product", action="store_true",
                     help="skip the one-launch-per-product comparison of the uneven batch")
     return ap.parse_args()
@@ -98,25 +98,12 @@ def measured_sm_max_mhz():
         return 2070.0
 
 
-def source_digest(paths):
-    h = hashlib.sha256()
-    for pth in paths:
-        with open(os.path.join(ROOT, pth), "rb") as f:
-            h.update(f.read())
-    return h.hexdigest()[:16]
-
-
 def recorded_traffic(kernel_key, n_elem):
-    """DRAM bytes per launch from the committed ncu summary, scaled to n_elem, or None
-    when the kernel source changed since the counters were taken."""
-    try:
-        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
-            rec = json.load(f)[kernel_key]
-    except Exception:
-        return None
-    if rec.get("source_digest") != source_digest(KERNEL_SOURCES):
-        return None
-    return rec["dram_bytes_per_launch"] * n_elem / rec["elements_per_launch"]
+    """DRAM bytes per launch from the committed ncu record (profiles/ncu_traffic.json),
+    scaled to n_elem, or None when the kernel's sources changed since the
+    counters were taken."""
+    import bench_polymul as bp
+    return bp.recorded_traffic(kernel_key, n_elem)
 
 
 class ClockSampler:
@@ -365,17 +352,32 @@ def run_gpu(args, ws, rank, local):
         t = cpu_oracle_step(arrays, n)
         cpu = {"value": 3 * 2 * n / t / 1e9, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                "sample": "one full step: 2^%d residues x 3 primes x {mont_mul, mont_fma}" % args.log2n}
+        n1 = min(n, 1 << 22)
+        with oracle.threads(1):
+            t1 = cpu_oracle_step(arrays, n1)
+        cpu["single_thread"] = {"value": 3 * 2 * n1 / t1 / 1e9, "unit": UNIT, "cores": 1,
+                                "sample": "first 2^%d residues of each operand, 3 primes x {mont_mul, mont_fma}"
+                                          % (n1.bit_length() - 1)}
 
     extra, errors = {}, {}
-    if rank == 0 and ws == 1:
+    if ws == 1 or args.sections_all_ranks:
+        # Each rank runs the sections on its own replica; rank 0 reports its own.
         import bench_polymul as bp
-        peaks = {"hbm_gbs": measured_peaks()[0], "sm_max_mhz": measured_sm_max_mhz()}
+        peaks = {"hbm_gbs": measured_peaks()[0], "sm_max_mhz": measured_sm_max_mhz(),
+                 "sms": torch.cuda.get_device_properties(local).multi_processor_count}
         secs = [x for x in args.sections.split(",") if x]
         sampler2 = ClockSampler(bus)
         sampler2.start()
-        cpu_on = not args.no_cpu_baseline
+        cpu_on = not args.no_cpu_baseline and ws == 1 and rank == 0
         cfg = tuple(int(x) for x in args.batch_config.split(",")) if args.batch_config else None
+
+        def probes():
+            res = bp.int_probes(m, torch)
+            peaks["probe_rates"] = {k: v["ops_per_s"] for k, v in res["kinds"].items()}
+            return res
+
         sections = [
+            ("probe", "int_probe", probes),
             ("roundtrip", "roundtrip_65536", lambda: bp.roundtrip_small(m, torch)),
             ("ntt", "ntt_fwd_inv", lambda: bp.ntt_transforms(m, torch, peaks)),
             ("uniform", "polymul_uniform_4096x2048", lambda: bp.uniform_batch(m, torch, peaks, cpu=cpu_on)),
@@ -388,10 +390,14 @@ def run_gpu(args, ws, rank, local):
         for name, key, fn in sections:
             if name in secs:
                 run_section(extra, errors, key, fn)
+        clk = sampler2.stop()
         if secs:
-            extra["clocks_polymul_sections"] = sampler2.stop()
-        else:
-            sampler2.stop()
+            extra["clocks_polymul_sections"] = clk
+        if "int_probe" in extra:
+            mhz = (clk or {}).get("sm_mhz") or peaks["sm_max_mhz"]
+            bp.probe_per_sm_clock(extra["int_probe"], mhz, peaks["sms"])
+        if ws > 1:
+            extra["sections_scope"] = "rank 0's replica (every rank ran the same sections on its own GPU)"
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

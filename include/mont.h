@@ -215,10 +215,14 @@ int polymul_many_ws(uint32_t p, const uint32_t *a, size_t la, const uint32_t *b,
  * la + lb - 1 must be <= 2^18 (else MONT_ERANGE; also MONT_ERANGE if the
  * plan's tables are too short).  Calls no cudaMalloc/cudaFree.  The first
  * call on each device looks up the array's device address
- * (cudaGetSymbolAddress): make that first call before any stream capture.
- * Every call on a device shares the one array, so calls whose kernels
- * overlap on the GPU (e.g. on different streams) race and must be ordered by
- * the caller; no state carries over from one call to the next.
+ * (cudaGetSymbolAddress) and keeps it for the life of the process: make that
+ * first call before any stream capture, and do not call this entry point
+ * again on a device after cudaDeviceReset (or anything else that destroys
+ * the device's primary context) in the same process, since the array may
+ * then sit at another address.  Every call on a device shares the one array,
+ * so calls whose kernels overlap on the GPU (e.g. on different streams) race
+ * and must be ordered by the caller; no state carries over from one call to
+ * the next.
  */
 int polymul_noalloc(const ntt_plan *plan, const uint32_t *a, size_t la, const uint32_t *b, size_t lb,
                     uint32_t *c, cudaStream_t stream);
@@ -400,6 +404,43 @@ int mont_server_get_stats(const mont_server *server, mont_server_stats *out);
 
 /* Frees the library-owned scratch buffers (waits for the device). */
 int mont_release_workspaces(void);
+
+/* ------------------------------------------------------------------------
+ * Measurement support: integer-pipe throughput probes.  (The paper reports
+ * no measurements; these give the roofline of Alg. 2's arithmetic and of the
+ * NTT butterflies built on it a measured ceiling on the device at hand.)
+ * ------------------------------------------------------------------------ */
+
+/* Probe kinds: one instruction form each (32-bit multiply-add, high-word
+ * multiply-add, 32x32->64 multiply-add, three-input add), one REDC (Alg. 2,
+ * result fully reduced), and the NTT butterflies as the transform kernels
+ * run them: Cooley-Tukey with a twiddle (REDC of y by w, lazy [0, 2P)
+ * values), with twiddle 1, with twiddle 1 on reduced inputs (level 0), and
+ * Gentleman-Sande with a twiddle and with twiddle 1. */
+enum {
+    MONT_PROBE_IMAD = 0,
+    MONT_PROBE_IMAD_HI = 1,
+    MONT_PROBE_IMAD_WIDE = 2,
+    MONT_PROBE_IADD3 = 3,
+    MONT_PROBE_REDC = 4,
+    MONT_PROBE_CT = 5,
+    MONT_PROBE_CT_ONE = 6,
+    MONT_PROBE_CT_FIRST = 7,
+    MONT_PROBE_GS = 8,
+    MONT_PROBE_GS_ONE = 9
+};
+
+/* Queues one probe kernel on `stream`: a grid of ctas_per_sm CTAs per SM
+ * (0 = as many as fit; 256 threads each), every thread applying the
+ * operation `kind` to 8 independent register chains 16 x iterations times,
+ * with no memory traffic.  *ops_per_launch (if not NULL) receives the number
+ * of operations the launch performs (instructions, REDCs or butterflies);
+ * divided by the launch's duration it is the throughput.  p: odd modulus,
+ * 3 <= p < 2^31, used by the REDC and butterfly kinds.  sink: a device word
+ * the kernel may write (keeps the chains live).  MONT_EINVAL for an unknown
+ * kind, a bad p, iterations == 0 or a NULL sink. */
+int mont_int_probe(int kind, uint32_t p, uint32_t iterations, uint32_t ctas_per_sm, uint32_t *sink,
+                   uint64_t *ops_per_launch, cudaStream_t stream);
 
 /* Static description of a return code; never NULL. */
 const char *mont_strerror(int code);

@@ -74,6 +74,8 @@ def lib():
                                        _u64p, ctypes.c_size_t, ctypes.c_int]
         L.or_polymul_batch.restype = ctypes.c_int
         L.or_num_threads.restype = ctypes.c_int
+        L.or_set_num_threads.argtypes = [ctypes.c_int]
+        L.or_set_num_threads.restype = None
         _lib = L
     return _lib
 
@@ -216,6 +218,23 @@ def polymul_batch(ps, a, a_off, la, b, b_off, lb, c_off, c_size, use_ntt=False):
 
 def num_threads():
     return lib().or_num_threads()
+
+
+class threads:
+    """Context manager: the oracle's OpenMP loops use n threads inside (for
+    timing it single-threaded), the previous count again after."""
+
+    def __init__(self, n):
+        self.n = int(n)
+
+    def __enter__(self):
+        self.prev = num_threads()
+        lib().or_set_num_threads(self.n)
+        return self
+
+    def __exit__(self, *exc):
+        lib().or_set_num_threads(self.prev)
+        return False
 
 
 __all__ = [n for n in dir() if not n.startswith("_")]

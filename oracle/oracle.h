@@ -91,6 +91,8 @@ int or_polymul_batch(const uint32_t *ps, const uint32_t *a, const uint64_t *a_of
 
 /* Threads an OpenMP region of this library uses. */
 int or_num_threads(void);
+/* Threads of the OpenMP loops from now on (n > 0); timing only. */
+void or_set_num_threads(int n);
 
 #ifdef __cplusplus
 }

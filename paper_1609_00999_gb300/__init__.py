@@ -16,3 +16,4 @@ from ._binding import (PolymulBatchConfig, PolymulBatchPlan, PolymulDesc,  # noq
                        polymul_batch_workspace_bytes)
 from ._binding import MontServer, MontServerStats, completion_dtype, request_dtype  # noqa: F401
 from ._binding import barrett_mulmod, check_residues, fourier_redc_mul  # noqa: F401
+from ._binding import PROBE_KINDS, int_probe  # noqa: F401

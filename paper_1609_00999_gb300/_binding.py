@@ -101,6 +101,9 @@ def _declare_ntt(L):
     _declare_server(L)
     L.mont_release_workspaces.argtypes = []
     L.mont_release_workspaces.restype = ctypes.c_int
+    L.mont_int_probe.argtypes = [ctypes.c_int, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _vp,
+                                 ctypes.POINTER(ctypes.c_uint64), _vp]
+    L.mont_int_probe.restype = ctypes.c_int
 
 
 class PolymulDesc(ctypes.Structure):
@@ -432,6 +435,20 @@ def polymul_noalloc(plan, a, b, out=None, stream=None):
     _check(lib().polymul_noalloc(plan.handle, _dev_ptr(a, "a"), a.numel(), _dev_ptr(b, "b"), b.numel(),
                                  _dev_ptr(out, "out"), _stream_handle(stream, a.device)), "polymul_noalloc")
     return out
+
+
+PROBE_KINDS = {"imad": 0, "imad_hi": 1, "imad_wide": 2, "iadd3": 3, "redc": 4, "ct": 5, "ct_one": 6,
+               "ct_first": 7, "gs": 8, "gs_one": 9}
+
+
+def int_probe(kind, p, iterations, sink, ctas_per_sm=0, stream=None):
+    """Queues one integer-pipe probe launch (``mont_int_probe``) of the named
+    kind (a key of PROBE_KINDS) and returns the number of operations it
+    performs; `sink` is a CUDA int32 tensor of at least one element."""
+    ops = ctypes.c_uint64(0)
+    _check(lib().mont_int_probe(PROBE_KINDS[kind], int(p), int(iterations), int(ctas_per_sm), _dev_ptr(sink, "sink"),
+                                ctypes.byref(ops), _stream_handle(stream, sink.device)), "mont_int_probe")
+    return int(ops.value)
 
 
 def _check_packed_bounds(na, a_off, la, nb, b_off, lb, nc, c_off):

@@ -64,10 +64,12 @@ __device__ __forceinline__ uint4 apply4(uint4 a, uint4 b, uint4 c, const EwParam
 
 // Vector body over n4 uint4 chunks plus a scalar tail of `tail` elements
 // starting at element 4 * n4.  For OP_SCALE, b is unused and k is the multiplier.
+// out may equal a, b or c (in place), so no pointer is __restrict__: each
+// element is read by the thread that writes it, before it writes it.
 template <int OP>
 __global__ void __launch_bounds__(kThreads)
-k_elementwise(const uint32_t *__restrict__ a, const uint32_t *__restrict__ b,
-              const uint32_t *__restrict__ c, uint32_t *__restrict__ out, size_t n4, uint32_t tail, EwParams q)
+k_elementwise(const uint32_t *a, const uint32_t *b, const uint32_t *c, uint32_t *out, size_t n4, uint32_t tail,
+              EwParams q)
 {
     const uint4 *a4 = reinterpret_cast<const uint4 *>(a);
     const uint4 *b4 = reinterpret_cast<const uint4 *>(b);
@@ -107,8 +109,7 @@ k_elementwise(const uint32_t *__restrict__ a, const uint32_t *__restrict__ b,
 // Scalar grid-stride variant for operands that are not all 16-byte aligned.
 template <int OP>
 __global__ void __launch_bounds__(kThreads)
-k_elementwise_scalar(const uint32_t *__restrict__ a, const uint32_t *__restrict__ b,
-                     const uint32_t *__restrict__ c, uint32_t *__restrict__ out, size_t n, EwParams q)
+k_elementwise_scalar(const uint32_t *a, const uint32_t *b, const uint32_t *c, uint32_t *out, size_t n, EwParams q)
 {
     const size_t stride = static_cast<size_t>(gridDim.x) * kThreads;
     for (size_t i = static_cast<size_t>(blockIdx.x) * kThreads + threadIdx.x; i < n; i += stride) {

@@ -100,3 +100,17 @@ def test_one_shot_batch_host_checks(L):
     bad = (m.PolymulDesc * 1)(desc(5, 0, 0))
     assert L.polymul_batch(bad, 1, ws, need, None) == m.MONT_EINVAL
     assert L.polymul_batch_check(None, None) == m.MONT_EINVAL
+
+
+def test_int_probe_argument_errors(L):
+    """The integer-pipe probe rejects bad arguments on the host, before any launch."""
+    import paper_1609_00999_gb300 as m
+    sink = ctypes.c_void_p(0x100000)
+    ops = ctypes.c_uint64(0)
+    assert L.mont_int_probe(99, synth.P1, 4, 1, sink, ctypes.byref(ops), None) == m.MONT_EINVAL   # unknown kind
+    assert L.mont_int_probe(-1, synth.P1, 4, 1, sink, ctypes.byref(ops), None) == m.MONT_EINVAL
+    assert L.mont_int_probe(4, synth.P1, 4, 1, None, ctypes.byref(ops), None) == m.MONT_EINVAL     # no sink
+    assert L.mont_int_probe(4, synth.P1, 0, 1, sink, ctypes.byref(ops), None) == m.MONT_EINVAL     # no work
+    for p in (0, 2, 2 ** 31 + 1):
+        assert L.mont_int_probe(4, p, 4, 1, sink, ctypes.byref(ops), None) == m.MONT_EINVAL
+    assert sorted(m.PROBE_KINDS.values()) == list(range(10))

@@ -56,6 +56,30 @@ def test_butterfly_classes_match_op_count(k):
     la, lb = n // 2, n // 2
     assert bp.int_ops_polymul(n, la, lb) == (2 * (10 * nontrivial + 4 * trivial) + 9 * nontrivial + 4 * trivial
                                              + 6 * n + 6 * lb)
+    # the operation classes the measured floor weights: level 0 (n/2
+    # butterflies, all in block 0, twiddle 1 on reduced inputs), the other
+    # twiddle-1 butterflies, and the rest
+    fwd = bp.op_counts_ntt(n, False)
+    assert fwd == {"ct": nontrivial, "ct_first": n // 2, "ct_one": trivial - n // 2}
+    assert bp.op_counts_ntt(n, True) == {"gs": nontrivial, "gs_one": trivial, "redc": n}
+    prod = bp.op_counts_polymul(n, lb)
+    assert prod == {"ct": 2 * nontrivial, "ct_first": n, "ct_one": 2 * (trivial - n // 2), "gs": nontrivial,
+                    "gs_one": trivial, "redc": n + lb}
+
+
+def test_measured_floor_arithmetic():
+    """floor = sum over classes of count / rate; frac = floor / time."""
+    counts = bp.add_counts({}, bp.op_counts_polymul(4096, 2048), 4096)
+    rates = {k: 1e12 for k in bp.OP_CLASSES}
+    floor = bp.floor_seconds(counts, rates)
+    assert floor == pytest.approx(sum(counts.values()) / 1e12)
+    peaks = {"sm_max_mhz": 2070.0, "sms": 152, "probe_rates": rates}
+    r = bp.int_roofline("k_polymul<12, RedAlg2>", 1e9, counts, 2 * floor * 1e3, peaks)
+    assert r["frac"] == pytest.approx(0.5) and r["peak_source"].startswith("measured")
+    assert r["achieved"] / r["peak"] == pytest.approx(0.5)
+    r2 = bp.int_roofline("k_polymul<12, RedAlg2>", 1e9, counts, 1.0, {"sm_max_mhz": 2070.0})
+    assert r2["peak_source"].startswith("derived")
+    assert bp.op_counts_polymul(1, 1) == {"redc": 2}
 
 
 def test_batch_hbm_bytes_pass_structure():
