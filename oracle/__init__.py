@@ -74,6 +74,11 @@ def lib():
                                        _u64p, ctypes.c_size_t, ctypes.c_int]
         L.or_polymul_batch.restype = ctypes.c_int
         L.or_num_threads.restype = ctypes.c_int
+        for name in ("or_tft", "or_itft"):
+            getattr(L, name).argtypes = [ctypes.c_uint32, _u32p, ctypes.c_size_t, ctypes.c_int, _u32p]
+            getattr(L, name).restype = ctypes.c_int
+        L.or_polymul_tft.argtypes = [ctypes.c_uint32, _u32p, ctypes.c_size_t, _u32p, ctypes.c_size_t, _u32p]
+        L.or_polymul_tft.restype = ctypes.c_int
         L.or_set_num_threads.argtypes = [ctypes.c_int]
         L.or_set_num_threads.restype = None
         _lib = L
@@ -198,6 +203,36 @@ def polymul_ntt(p, a, b):
         raise ValueError("oracle: empty operand")
     c = np.empty(a.size + b.size - 1, dtype=np.uint32)
     if lib().or_polymul_ntt(p, _ptr(a), a.size, _ptr(b), b.size, _ptr(c)) != 0:
+        raise ValueError("oracle: product too long for P")
+    return c
+
+
+def tft(p, x, log2n):
+    """Truncated Fourier transform (van der Hoeven): the first len(x) outputs,
+    in bit-reversed order, of the size-2^log2n transform of x zero-padded."""
+    x = _u32(x)
+    out = np.empty_like(x)
+    if lib().or_tft(p, _ptr(x), x.size, int(log2n), _ptr(out)) != 0:
+        raise ValueError("oracle: bad TFT length %d for 2^%d mod %d" % (x.size, log2n, p))
+    return out
+
+
+def itft(p, y, log2n):
+    """Inverse truncated Fourier transform: the x (len(y) entries) with tft(x) == y."""
+    y = _u32(y)
+    out = np.empty_like(y)
+    if lib().or_itft(p, _ptr(y), y.size, int(log2n), _ptr(out)) != 0:
+        raise ValueError("oracle: bad TFT length %d for 2^%d mod %d" % (y.size, log2n, p))
+    return out
+
+
+def polymul_tft(p, a, b):
+    """a * b through TFTs of length len(a) + len(b) - 1."""
+    a, b = _u32(a), _u32(b)
+    if a.size == 0 or b.size == 0:
+        raise ValueError("oracle: empty operand")
+    c = np.empty(a.size + b.size - 1, dtype=np.uint32)
+    if lib().or_polymul_tft(p, _ptr(a), a.size, _ptr(b), b.size, _ptr(c)) != 0:
         raise ValueError("oracle: product too long for P")
     return c
 

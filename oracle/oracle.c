@@ -243,6 +243,139 @@ int or_polymul_ntt(uint32_t p, const uint32_t *a, size_t la, const uint32_t *b, 
     return 0;
 }
 
+/*
+ * Truncated Fourier transform (J. van der Hoeven, "The truncated Fourier
+ * transform and applications", ISSAC 2004; the paper cites TFT-based
+ * polynomial libraries in Sec. 1).  The size-N = 2^K transform is taken in
+ * its in-place Cooley-Tukey form: level s = 0 .. K-1 splits the array into
+ * 2^s blocks of 2h = N / 2^s entries, and block i pairs (j, j + h) with the
+ * twiddle r = w^(brev_s(i) h):  (x, y) -> (x + r y, x - r y).  After level
+ * K-1, position q holds X_{brev_K(q)}.  The TFT of x (l entries, zero beyond)
+ * is the first l positions of that output; it computes, at each level, only
+ * the entries that the remaining levels need to produce them.  Arithmetic by
+ * 64-bit `%`, as everywhere in this file.
+ */
+static uint64_t brev_bits(uint64_t i, int bits)
+{
+    uint64_t r = 0;
+    for (int b = 0; b < bits; b++) r |= ((i >> b) & 1u) << (bits - 1 - b);
+    return r;
+}
+
+static uint32_t addmod(uint32_t a, uint32_t b, uint32_t p)
+{
+    return (uint32_t)(((uint64_t)a + b) % p);
+}
+
+static uint32_t submod(uint32_t a, uint32_t b, uint32_t p)
+{
+    return (uint32_t)(((uint64_t)a + p - b) % p);
+}
+
+int or_tft(uint32_t p, const uint32_t *x, size_t l, int log2n, uint32_t *out)
+{
+    if (log2n < 0 || log2n > 30) return -1;
+    const size_t n = (size_t)1 << log2n;
+    if (l == 0 || l > n) return -1;
+    const uint32_t w = or_root_of_unity(p, n, 0);
+    if (w == 0) return -1;
+    uint32_t *a = (uint32_t *)calloc(n, sizeof(uint32_t));
+    if (!a) return -1;
+    memcpy(a, x, l * sizeof(uint32_t));
+    for (int s = 0; s < log2n; s++) {
+        const size_t h = n >> (s + 1);
+        const size_t need = (l + h - 1) / h * h;   /* entries later levels read */
+        for (size_t b = 0; b < need; b += 2 * h) {
+            const uint32_t r = or_powmod(w, brev_bits(b / (2 * h), s) * h, p);
+            for (size_t j = b; j < b + h; j++) {
+                const uint32_t u = a[j], v = or_mulmod(a[j + h], r, p);
+                a[j] = addmod(u, v, p);
+                if (j + h < need) a[j + h] = submod(u, v, p);
+            }
+        }
+    }
+    memcpy(out, a, l * sizeof(uint32_t));
+    free(a);
+    return 0;
+}
+
+/*
+ * Inverse TFT (van der Hoeven's recursion).  Node: block i of level s,
+ * `size` = N / 2^s entries at a[0 .. size).  On entry a[0 .. l) holds the
+ * node's transform outputs and a[l .. size) its (known) level-s inputs; on
+ * return a[0 .. size) holds all of its level-s inputs.  With h = size / 2
+ * and r the node's twiddle, the level-s butterfly gives the left child
+ * u_j = x_j + r x_{j+h} and the right child v_j = x_j - r x_{j+h}:
+ *  - l >= h: the left child's outputs are all known, so its inputs u follow
+ *    by recursion; for j >= l - h the right child's input is known too,
+ *    v_j = u_j - 2 r x_{j+h}; recursion on the right child gives the other
+ *    v_j; then x_j = (u_j + v_j) / 2, x_{j+h} = (u_j - v_j) / (2r).
+ *  - l < h: for j >= l the left child's input u_j = x_j + r x_{j+h} is
+ *    known; recursion on the left child gives u_j for j < l, and then
+ *    x_j = u_j - r x_{j+h}.
+ */
+static void itft_node(uint32_t p, uint32_t *a, size_t size, int s, uint64_t i, size_t l, uint32_t w, int log2n,
+                      uint32_t inv2)
+{
+    if (size == 1 || l == 0) return;
+    const size_t h = size / 2;
+    const uint32_t r = or_powmod(w, brev_bits(i, s) * ((uint64_t)1 << (log2n - s - 1)), p);
+    if (l >= h) {
+        itft_node(p, a, h, s + 1, 2 * i, h, w, log2n, inv2);
+        for (size_t j = l - h; j < h; j++) a[h + j] = submod(a[j], or_mulmod(2 % p, or_mulmod(r, a[h + j], p), p), p);
+        itft_node(p, a + h, h, s + 1, 2 * i + 1, l - h, w, log2n, inv2);
+        const uint32_t inv2r = or_mulmod(inv2, (uint32_t)or_invmod(r, p), p);
+        for (size_t j = 0; j < h; j++) {
+            const uint32_t u = a[j], v = a[h + j];
+            a[j] = or_mulmod(addmod(u, v, p), inv2, p);
+            a[h + j] = or_mulmod(submod(u, v, p), inv2r, p);
+        }
+    } else {
+        for (size_t j = l; j < h; j++) a[j] = addmod(a[j], or_mulmod(r, a[h + j], p), p);
+        itft_node(p, a, h, s + 1, 2 * i, l, w, log2n, inv2);
+        for (size_t j = 0; j < h; j++) a[j] = submod(a[j], or_mulmod(r, a[h + j], p), p);
+    }
+}
+
+int or_itft(uint32_t p, const uint32_t *y, size_t l, int log2n, uint32_t *out)
+{
+    if (log2n < 0 || log2n > 30) return -1;
+    const size_t n = (size_t)1 << log2n;
+    if (l == 0 || l > n) return -1;
+    const uint32_t w = or_root_of_unity(p, n, 0);
+    if (w == 0) return -1;
+    uint32_t *a = (uint32_t *)calloc(n, sizeof(uint32_t));   /* inputs beyond l are zero */
+    if (!a) return -1;
+    memcpy(a, y, l * sizeof(uint32_t));
+    itft_node(p, a, n, 0, 0, l, w, log2n, (uint32_t)((p + 1u) / 2u));
+    memcpy(out, a, l * sizeof(uint32_t));
+    free(a);
+    return 0;
+}
+
+/* c = a * b through TFTs of length l = la + lb - 1 in the transform of size
+ * 2^ceil(log2 l): the first l outputs of both operands, their pointwise
+ * products (the TFT of c, whose degree is below l) and the inverse TFT. */
+int or_polymul_tft(uint32_t p, const uint32_t *a, size_t la, const uint32_t *b, size_t lb, uint32_t *c)
+{
+    if (la == 0 || lb == 0) return -1;
+    const size_t l = la + lb - 1;
+    int k = 0;
+    while (((size_t)1 << k) < l) k++;
+    uint32_t *buf = (uint32_t *)calloc(3 * l, sizeof(uint32_t));
+    if (!buf) return -1;
+    uint32_t *pa = buf, *pb = buf + l, *t = buf + 2 * l;
+    memcpy(t, a, la * sizeof(uint32_t));
+    int rc = or_tft(p, t, l, k, pa);
+    memset(t, 0, l * sizeof(uint32_t));
+    memcpy(t, b, lb * sizeof(uint32_t));
+    if (rc == 0) rc = or_tft(p, t, l, k, pb);
+    for (size_t q = 0; q < l && rc == 0; q++) pa[q] = or_mulmod(pa[q], pb[q], p);
+    if (rc == 0) rc = or_itft(p, pa, l, k, c);
+    free(buf);
+    return rc;
+}
+
 int or_polymul_batch(const uint32_t *ps, const uint32_t *a, const uint64_t *a_off, const uint64_t *la,
                      const uint32_t *b, const uint64_t *b_off, const uint64_t *lb, uint32_t *c,
                      const uint64_t *c_off, size_t count, int use_ntt)

@@ -90,6 +90,15 @@ int or_polymul_batch(const uint32_t *ps, const uint32_t *a, const uint64_t *a_of
                      const uint64_t *c_off, size_t count, int use_ntt);
 
 /* Threads an OpenMP region of this library uses. */
+/* Truncated Fourier transform (van der Hoeven 2004) of x (l entries, zero
+ * beyond) in the transform of size N = 2^log2n >= l: out[q] = X_{brev(q)}
+ * for q < l, X the DFT of the zero-padded x (the in-place Cooley-Tukey
+ * output order).  -1 for l == 0, l > N or no N-th root of unity mod p. */
+int or_tft(uint32_t p, const uint32_t *x, size_t l, int log2n, uint32_t *out);
+/* Inverse: the x (l entries, zero beyond) whose TFT is y. */
+int or_itft(uint32_t p, const uint32_t *y, size_t l, int log2n, uint32_t *out);
+/* c = a * b (la + lb - 1 entries) through TFTs of length la + lb - 1. */
+int or_polymul_tft(uint32_t p, const uint32_t *a, size_t la, const uint32_t *b, size_t lb, uint32_t *c);
 int or_num_threads(void);
 /* Threads of the OpenMP loops from now on (n > 0); timing only. */
 void or_set_num_threads(int n);

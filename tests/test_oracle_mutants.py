@@ -62,6 +62,17 @@ MUTANTS = [
     ("schoolbook_no_accumulate", "c[i + j] = (uint32_t)(((uint64_t)c[i + j] + or_mulmod(a[i], b[j], p)) % p);",
      "c[i + j] = or_mulmod(a[i], b[j], p);"),
     ("mulmod_vec_squares_x", "out[i] = or_mulmod(x[i], y[i], p);", "out[i] = or_mulmod(x[i], x[i], p);"),
+    ("tft_needed_entries_rounded_down", "const size_t need = (l + h - 1) / h * h;",
+     "const size_t need = l / h * h + (l < h ? h : 0);"),
+    ("tft_twiddle_not_bit_reversed", "or_powmod(w, brev_bits(b / (2 * h), s) * h, p)", "or_powmod(w, (b / (2 * h)) * h, p)"),
+    ("itft_right_tail_plus", "a[h + j] = submod(a[j], or_mulmod(2 % p, or_mulmod(r, a[h + j], p), p), p);",
+     "a[h + j] = addmod(a[j], or_mulmod(2 % p, or_mulmod(r, a[h + j], p), p), p);"),
+    ("itft_half_dropped", "a[j] = or_mulmod(addmod(u, v, p), inv2, p);", "a[j] = addmod(u, v, p);"),
+    ("itft_left_tail_minus", "for (size_t j = l; j < h; j++) a[j] = addmod(a[j], or_mulmod(r, a[h + j], p), p);",
+     "for (size_t j = l; j < h; j++) a[j] = submod(a[j], or_mulmod(r, a[h + j], p), p);"),
+    ("itft_twiddle_of_parent_level", "((uint64_t)1 << (log2n - s - 1))", "((uint64_t)1 << (log2n - s))"),
+    ("polymul_tft_b_transform_into_a", "if (rc == 0) rc = or_tft(p, t, l, k, pb);",
+     "if (rc == 0) rc = or_tft(p, t, l, k, pa);"),
 ]
 
 

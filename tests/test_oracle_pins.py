@@ -191,6 +191,11 @@ def test_golden_examples():
             assert oracle.mont_mul(p, [int(args[0])], [int(args[1])]).tolist() == expected
         elif kind == "to_mont":
             assert oracle.to_mont(p, [int(args[0])]).tolist() == expected
+        elif kind == "tft":
+            k = int(args[0])
+            x = [int(v) for v in args[1].split(",")]
+            assert oracle.tft(p, x, k).tolist() == expected
+            assert oracle.itft(p, expected, k).tolist() == x
         else:
             raise AssertionError(kind)
 
@@ -372,3 +377,58 @@ def test_polymul_batch_matches_single_products():
             co = int(wl.c_off[i])
             ref = _kronecker(wl.a[ao:ao + la].tolist(), wl.b[bo:bo + lb].tolist(), int(wl.primes[i]))
             assert c[co:co + la + lb - 1].tolist() == ref
+
+
+# ---------------------------------------------------------------- truncated Fourier transform
+
+def _brev(i, bits):
+    return int(format(i, "0%db" % bits)[::-1], 2) if bits else 0
+
+
+@pytest.mark.parametrize("p", synth.PRIMES)
+def test_tft_is_the_truncated_dft(p):
+    """For every N = 2^K <= 2^10 and every length 1 <= l <= N: the TFT of x
+    (l entries) is X_brev(q), q < l, where X_k = sum_{j<l} x_j w^(jk) is
+    summed here from the definition (prefix sums over j, in numpy), not by
+    any oracle routine."""
+    for k in range(0, 11):
+        n = 1 << k
+        w = int(oracle.root_of_unity(p, n)) if n > 1 else 1
+        wpow = np.ones(n, dtype=np.uint64)
+        for e in range(1, n):
+            wpow[e] = wpow[e - 1] * w % p
+        x = synth.residues(n, p, 97, k).astype(np.uint64)
+        idx = np.arange(n, dtype=np.uint64)
+        order = np.array([_brev(q, k) for q in range(n)])
+        X = np.zeros(n, dtype=np.uint64)
+        for l in range(1, n + 1):
+            j = l - 1
+            X = (X + x[j] * wpow[(j * idx) % n]) % p
+            got = oracle.tft(p, x[:l].astype(np.uint32), k)
+            assert np.array_equal(got, X[order[:l]].astype(np.uint32)), (k, l)
+
+
+@pytest.mark.parametrize("p", synth.PRIMES)
+def test_itft_inverts_tft(p):
+    """ITFT(TFT(x)) = x for every l <= N <= 2^10, and TFT(ITFT(y)) = y for
+    arbitrary y (the l evaluation points are distinct, so the TFT is a
+    bijection on length-l vectors)."""
+    for k in range(0, 11):
+        n = 1 << k
+        for l in range(1, n + 1):
+            x = synth.residues(l, p, 98, k, l, 0)
+            assert np.array_equal(oracle.itft(p, oracle.tft(p, x, k), k), x), (k, l)
+            if l % 7 == 1 or l == n:
+                y = synth.residues(l, p, 98, k, l, 1)
+                assert np.array_equal(oracle.tft(p, oracle.itft(p, y, k), k), y), (k, l)
+
+
+@pytest.mark.parametrize("p", synth.PRIMES + (17, 97))
+@pytest.mark.parametrize("la,lb", [(1, 1), (1, 2), (2, 2), (3, 2), (5, 5), (9, 8), (31, 17), (33, 32),
+                                   (64, 65), (100, 3), (130, 129), (257, 255)])
+def test_polymul_tft_against_big_integers(p, la, lb):
+    if (p - 1) % (1 << (la + lb - 2).bit_length()) != 0:
+        pytest.skip("no root of unity of that order")
+    a = synth.residues(la, p, 99, la, lb, 0)
+    b = synth.residues(lb, p, 99, la, lb, 1)
+    assert oracle.polymul_tft(p, a, b).tolist() == _kronecker(a.tolist(), b.tolist(), p)
