@@ -9,7 +9,8 @@
 // the transform kernels inline them (ntt_core.cuh).  Chains that would fold
 // under algebraic simplification (repeated adds, repeated butterflies with
 // twiddle 1 on unreduced values) take an operand from the neighbouring
-// chain, so each step stays one operation.
+// chain, and the level-0 butterfly (adds only) passes its results through an
+// empty asm, so each step stays one operation.
 //
 // The benchmark times each probe with CUDA events; operations per second
 // over the whole GPU are the ceiling the roofline of the transform and
@@ -59,7 +60,11 @@ __device__ __forceinline__ void probe_step(uint32_t (&x)[kChains], uint32_t (&y)
         } else if constexpr (KIND == MONT_PROBE_CT_ONE) {
             bfly_ct_one(x[i], y[j], m);
         } else if constexpr (KIND == MONT_PROBE_CT_FIRST) {
+            // Two adds with no reduction: repeated steps are linear in the
+            // starting values, so an empty asm hides each result from the
+            // compiler's algebra (no instruction is emitted for it).
             bfly_ct_first(x[i], y[j], m);
+            asm("" : "+r"(x[i]), "+r"(y[j]));
         } else if constexpr (KIND == MONT_PROBE_GS) {
             bfly_gs<RedAlg2>(x[i], y[i], w[i], m);
         } else if constexpr (KIND == MONT_PROBE_GS_ONE) {
