@@ -199,21 +199,49 @@ def probe_per_sm_clock(section, sm_mhz, sms):
     return section
 
 
-def batch_hbm_bytes(n, la, lb):
+ROW_LOG = 13   # rows of 2^13 in the batch kernel's split products
+
+
+def tft_rows(n, lc):
+    """Rows of 2^13 a batch product of size n computes when it runs as a
+    row-granular truncated transform (the batch builder's rule: 2 <= log2 n -
+    13 <= 4 and ceil(lc / 2^13) leaves rows unused), else None."""
+    k1 = n.bit_length() - 1 - ROW_LOG
+    if 2 <= k1 <= 4:
+        need = -(-lc // (1 << ROW_LOG))
+        if need < (1 << k1):
+            return need
+    return None
+
+
+def skipped_row_ops(n, rows):
+    """(operation counts, lane-ops) of the rows a truncated product does not
+    compute: per row, the forward row levels of both operands and the
+    inverse row levels (13 levels of 2^12 butterflies, all with a twiddle in
+    rows 1 and up) and its 2^13 pointwise REDCs."""
+    skipped = (n >> ROW_LOG) - rows
+    per = (1 << (ROW_LOG - 1)) * ROW_LOG
+    counts = {"ct": -2 * per * skipped, "gs": -per * skipped, "redc": -(1 << ROW_LOG) * skipped}
+    return counts, -skipped * ((2 * 10 + 9) * per + 6 * (1 << ROW_LOG))
+
+
+def batch_hbm_bytes(n, la, lb, rows=None):
     """Algorithmic HBM bytes of one product of size n in the batch kernel:
     operands in and result out; products of 2^14 and 2^15 (whole-product
     jobs) also read their operands once per row (2 or 4 rows) and pass their
     product rows through scratch (n words out and back); larger ones move
     2n words of forward scratch out and back, n words of product rows out
-    and back."""
+    and back.  A truncated product computing `rows` rows of 2^13 moves the
+    scratch of those rows only."""
     lc = la + lb - 1
     io = 4 * (la + lb + lc)
     if n <= 1 << 13:
         return io
-    if n <= 1 << 15:
+    if rows is None:
         rows = n >> 13
-        return io + 4 * (rows - 1) * (la + lb) + 4 * 2 * n
-    return io + 4 * (2 * 2 * n + 2 * n)
+    if n <= 1 << 15:
+        return io + 4 * (rows - 1) * (la + lb) + 4 * 2 * (rows << 13)
+    return io + 4 * 6 * (rows << 13)
 
 
 def _events(torch):
@@ -460,6 +488,9 @@ def reduction_ab(m, torch, steps=20, warmup=3):
 
 
 def uneven_batch(m, torch, peaks, steps=10, warmup=3, cpu=True, per_product=True, config=None):
+    """The 10,000-product uneven workload in one persistent launch replayed
+    from a CUDA graph: tuned (truncated transforms on, the default), then the
+    same launch shape with every product padded to its full transform."""
     import oracle
     wl = synth.batch_uneven()
     da = torch.from_numpy(wl.a.view(np.int32)).cuda()
@@ -473,45 +504,81 @@ def uneven_batch(m, torch, peaks, steps=10, warmup=3, cpu=True, per_product=True
         plan.config = m.PolymulBatchConfig(*config)
         cfg = plan.config
     tune_s = time.perf_counter() - t0
-    for _ in range(warmup):
-        plan.run_graph()
-    torch.cuda.synchronize()
-    e0, e1 = _events(torch)
-    e0.record()
-    for _ in range(steps):
-        plan.run_graph()
-    e1.record()
-    e1.synchronize()
-    assert plan.status() == m.MONT_OK
-    ms = e0.elapsed_time(e1) / steps
+
+    def timed():
+        for _ in range(warmup):
+            plan.run_graph()
+        torch.cuda.synchronize()
+        e0, e1 = _events(torch)
+        e0.record()
+        for _ in range(steps):
+            plan.run_graph()
+        e1.record()
+        e1.synchronize()
+        assert plan.status() == m.MONT_OK
+        return e0.elapsed_time(e1) / steps
+
+    ms = timed()
+    got = dc.cpu().numpy().view(np.uint32)
+    c_full = m.PolymulBatchConfig(cfg.ctas_per_sm, cfg.order, cfg.kernel, 1)
+    plan.config = c_full
+    dc.fill_(-1)
+    ms_full = timed()
+    got_full = dc.cpu().numpy().view(np.uint32)
+    plan.config = cfg
     coeffs = float((wl.la + wl.lb).sum())
-    ns = [1 << int(lc - 1).bit_length() for lc in (wl.la + wl.lb - 1)]
-    ops = float(sum(int_ops_polymul(n, int(la), int(lb)) for n, la, lb in zip(ns, wl.la, wl.lb)))
-    counts = {}
-    for n, lb in zip(ns, wl.lb):
-        add_counts(counts, op_counts_polymul(n, int(lb)))
-    hbm = float(sum(batch_hbm_bytes(n, int(la), int(lb)) for n, la, lb in zip(ns, wl.la, wl.lb)))
+    lcs = (wl.la + wl.lb - 1).astype(np.int64)
+    ns = [1 << int(lc - 1).bit_length() for lc in lcs]
+
+    def work(truncated):
+        ops, hbm, counts = 0.0, 0.0, {}
+        for n, la, lb, lc in zip(ns, wl.la, wl.lb, lcs):
+            rows = tft_rows(n, int(lc)) if truncated else None
+            add_counts(counts, op_counts_polymul(n, int(lb)))
+            ops += int_ops_polymul(n, int(la), int(lb))
+            if rows is not None:
+                c_skip, ops_skip = skipped_row_ops(n, rows)
+                add_counts(counts, c_skip)
+                ops += ops_skip
+            hbm += batch_hbm_bytes(n, int(la), int(lb), rows)
+        return ops, hbm, counts
+
+    def figures(t_ms, truncated):
+        ops, hbm, counts = work(truncated)
+        return {"ms": t_ms, "value": coeffs / t_ms / 1e6, "unit": "Gcoef/s",
+                "roofline": int_roofline("k_polymul_batch", ops, counts, t_ms, peaks,
+                                         traffic_units=len(wl) if truncated else None),
+                "hbm_at_pass_count": {"bytes": hbm, "achieved_gbs": hbm / (t_ms / 1e3) / 1e9,
+                                      "peak_gbs": peaks["hbm_gbs"],
+                                      "frac": hbm / (t_ms / 1e3) / 1e9 / peaks["hbm_gbs"]}}
+
+    tft = figures(ms, True)
+    full = figures(ms_full, False)
+    n_trunc = sum(1 for n, lc in zip(ns, lcs) if tft_rows(n, int(lc)) is not None)
     res = {"workload": "10,000 products, L log-uniform in [2^6, 2^16], primes uniform from "
                        "{2013265921, 469762049, 754974721}, N padded to powers of two",
-           "value": coeffs / ms / 1e6, "unit": "Gcoef/s", "ms": ms, "steps": steps, "warmup": warmup,
+           "value": tft["value"], "unit": "Gcoef/s", "ms": ms, "steps": steps, "warmup": warmup,
            "launch": "one persistent kernel per batch, replayed from a CUDA graph",
            "tuned_config": {"ctas_per_sm": cfg.ctas_per_sm, "order": cfg.order, "kernel": cfg.kernel,
-                            "tuned": config is None}, "tune_s": tune_s,
+                            "full_transforms": cfg.full_transforms, "tuned": config is None}, "tune_s": tune_s,
            "workspace_bytes": plan.workspace_bytes(), "l2": "operands + scratch (2.4 GB) larger than L2",
-           "gpu_launches": steps,
-           "roofline": int_roofline("k_polymul_batch", ops, counts, ms, peaks, traffic_units=len(wl)),
-           "hbm_at_pass_count": {"bytes": hbm, "achieved_gbs": hbm / (ms / 1e3) / 1e9, "peak_gbs": peaks["hbm_gbs"],
-                                 "frac": hbm / (ms / 1e3) / 1e9 / peaks["hbm_gbs"],
-                                 "passes": "one for N <= 2^13; operands, results and the product rows' scratch "
-                                           "round trip for 2^14 and 2^15 (operands read 2 or 4 times); "
-                                           "three passes through 2N words of scratch above"}}
-    got = dc.cpu().numpy().view(np.uint32)
+           "gpu_launches": 2 * (steps + warmup),
+           "roofline": tft["roofline"],
+           "hbm_at_pass_count": dict(tft["hbm_at_pass_count"],
+                                     passes="one for N <= 2^13; operands, results and the product rows' scratch "
+                                            "round trip for 2^14 and 2^15 (operands read once per row); three "
+                                            "passes through the scratch of the rows computed above"),
+           "truncated_products": n_trunc,
+           "full_transforms": dict(full, note="same launch shape, every product padded to its full power-of-two "
+                                              "transform (polymul_batch_config.full_transforms = 1)"),
+           "full_over_truncated_time": ms_full / ms}
     if not cpu:
         for i in (0, 1, 9999):
             ao, la, bo, lb, co = (int(wl.a_off[i]), int(wl.la[i]), int(wl.b_off[i]), int(wl.lb[i]), int(wl.c_off[i]))
             ref = oracle.polymul_ntt(int(wl.primes[i]), wl.a[ao:ao + la], wl.b[bo:bo + lb])
             assert np.array_equal(got[co:co + la + lb - 1], ref), "batch parity spot check failed"
-        res["parity"] = "products 0, 1 and 9999 equal to the oracle's"
+            assert np.array_equal(got_full[co:co + la + lb - 1], ref), "batch parity spot check failed"
+        res["parity"] = "products 0, 1 and 9999 (truncated and full transforms) equal to the oracle's"
     if per_product:
         L = m.lib()
         stream = torch.cuda.current_stream().cuda_stream
@@ -537,13 +604,15 @@ def uneven_batch(m, torch, peaks, steps=10, warmup=3, cpu=True, per_product=True
         res["batched_over_per_product"] = one_ms / ms
     if cpu:
         # The CPU baseline computes all 10,000 products; its result is also
-        # the parity check of every output word of the batch.
+        # the parity check of every output word of both batch variants.
         t0 = time.perf_counter()
         ref = oracle.polymul_batch(wl.primes, wl.a, wl.a_off, wl.la, wl.b, wl.b_off, wl.lb, wl.c_off, wl.c_size,
                                    use_ntt=True)
         t = time.perf_counter() - t0
-        assert np.array_equal(got[:wl.c_size], ref), "batch parity check failed"
-        res["parity"] = "every output word of all 10,000 products equal to the oracle's"
+        assert np.array_equal(got[:wl.c_size], ref), "batch parity check failed (truncated transforms)"
+        assert np.array_equal(got_full[:wl.c_size], ref), "batch parity check failed (full transforms)"
+        res["parity"] = ("every output word of all 10,000 products equal to the oracle's, with truncated and "
+                         "with full transforms")
         res["cpu_baseline"] = {"value": coeffs / t / 1e9, "unit": "Gcoef/s",
                                "cores": oracle.num_threads(), "kind": "oracle",
                                "sample": "all 10,000 products (oracle radix-2 NTT, OpenMP over products)"}

@@ -246,7 +246,14 @@ typedef struct polymul_desc {
 } polymul_desc;
 
 /* Launch shape of a batch: CTAs per SM of the persistent grid (0 = as many
- * as fit), the job order and the kernel variant.  Products up to 2^13 run
+ * as fit), the job order, the kernel variant and the transform form.
+ * Truncated transforms (the TFT of J. van der Hoeven, "The truncated Fourier
+ * transform and applications", 2004, which the polynomial libraries of
+ * Sec. 1 use to avoid power-of-two padding): a product of N = 2^K, split into
+ * 2^(K-13) rows of 2^13, computes only the first ceil((la + lb - 1) / 2^13)
+ * rows of the forward transforms (the first outputs in bit-reversed order)
+ * and recovers c from them by an inverse TFT over each column; the results
+ * are the same, bit for bit.  Products up to 2^13 run
  * whole in one CTA, products of 2^14 and 2^15 as one whole-product job each,
  * larger ones as column-tile, row and output-tile jobs.  Orders: 0: column
  * tiles first, then whole-product and small jobs, then rows and output
@@ -256,7 +263,10 @@ typedef struct polymul_desc {
 typedef struct polymul_batch_config {
     int ctas_per_sm;
     int order;
-    int kernel;   /* 0: registers budgeted for 2 CTAs per SM; 1: for 3 CTAs per SM */
+    int kernel;            /* 0: registers budgeted for 2 CTAs per SM; 1: for 3 CTAs per SM */
+    int full_transforms;   /* 0 (default): products of N = 2^15 .. 2^17 whose length leaves rows of
+                              2^13 unused run as truncated transforms (below); 1: every product is
+                              padded to its full power-of-two transform */
 } polymul_batch_config;
 
 /* Library-owned plan: device copies of the job list and the product table,
@@ -275,12 +285,13 @@ int polymul_batch_plan_create(const polymul_desc *descs, size_t count, polymul_b
  * 2: row; 3: output tile; 4: whole product), log2 N, product, and the tile
  * or row index (kind 0: the product count).  Products are numbered in the
  * kernel's order (single-CTA products first, by size, then the others in
- * descriptor order); prods, if not NULL, receives 3 words per product:
- * log2 N, column tiles, rows.  *njobs gets the full job count.  Errors as
- * polymul_batch_plan_create's descriptor checks; MONT_EINVAL for a bad
- * order. */
-int polymul_batch_describe(const polymul_desc *descs, size_t count, int order, uint32_t *jobs, size_t cap,
-                           uint32_t *prods, size_t *njobs);
+ * descriptor order); prods, if not NULL, receives 4 words per product:
+ * log2 N, column tiles, rows computed, and 1 if the product runs as a
+ * truncated transform.  full_transforms as in polymul_batch_config.
+ * *njobs gets the full job count.  Errors as polymul_batch_plan_create's
+ * descriptor checks; MONT_EINVAL for a bad order or full_transforms. */
+int polymul_batch_describe(const polymul_desc *descs, size_t count, int order, int full_transforms, uint32_t *jobs,
+                           size_t cap, uint32_t *prods, size_t *njobs);
 void polymul_batch_plan_destroy(polymul_batch_plan *plan);
 size_t polymul_batch_plan_workspace_bytes(const polymul_batch_plan *plan);
 int polymul_batch_plan_get_config(const polymul_batch_plan *plan, polymul_batch_config *cfg);

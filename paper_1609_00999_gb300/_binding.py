@@ -114,17 +114,18 @@ class PolymulDesc(ctypes.Structure):
 
 class PolymulBatchConfig(ctypes.Structure):
     """Mirror of ``polymul_batch_config``."""
-    _fields_ = [("ctas_per_sm", ctypes.c_int), ("order", ctypes.c_int), ("kernel", ctypes.c_int)]
+    _fields_ = [("ctas_per_sm", ctypes.c_int), ("order", ctypes.c_int), ("kernel", ctypes.c_int),
+                ("full_transforms", ctypes.c_int)]
 
     def __repr__(self):
-        return "PolymulBatchConfig(ctas_per_sm=%d, order=%d, kernel=%d)" % (self.ctas_per_sm, self.order,
-                                                                            self.kernel)
+        return "PolymulBatchConfig(ctas_per_sm=%d, order=%d, kernel=%d, full_transforms=%d)" % (
+            self.ctas_per_sm, self.order, self.kernel, self.full_transforms)
 
 
 def _declare_batch(L):
     vpp = ctypes.POINTER(_vp)
     L.polymul_batch_plan_create.argtypes = [ctypes.POINTER(PolymulDesc), _sz, vpp]
-    L.polymul_batch_describe.argtypes = [ctypes.POINTER(PolymulDesc), _sz, ctypes.c_int, _vp, _sz, _vp,
+    L.polymul_batch_describe.argtypes = [ctypes.POINTER(PolymulDesc), _sz, ctypes.c_int, ctypes.c_int, _vp, _sz, _vp,
                                          ctypes.POINTER(_sz)]
     L.polymul_batch_describe.restype = ctypes.c_int
     L.polymul_batch_plan_destroy.argtypes = [_vp]
@@ -548,21 +549,22 @@ def polymul_batch_plan_create(descs, keepalive=()):
     return PolymulBatchPlan(descs, keepalive)
 
 
-def polymul_batch_describe(descs, order):
+def polymul_batch_describe(descs, order, full_transforms=0):
     """Host only: (jobs [n][4] uint32: kind, log2 N, product, index;
-    prods [count][3] uint32: log2 N, column tiles, rows) of the job list the
-    batch kernel runs for these descriptors in job order `order`."""
+    prods [count][4] uint32: log2 N, column tiles, rows computed, truncated
+    transform flag) of the job list the batch kernel runs for these
+    descriptors in job order `order`."""
     import numpy as np
     arr = (PolymulDesc * max(1, len(descs)))()
     for i, d in enumerate(descs):
         arr[i] = d
     n = _sz(0)
-    _check(lib().polymul_batch_describe(arr, len(descs), int(order), None, 0, None, ctypes.byref(n)),
-           "polymul_batch_describe")
-    jobs = np.zeros((max(1, n.value), 4), dtype=np.uint32)
-    prods = np.zeros((max(1, len(descs)), 3), dtype=np.uint32)
-    _check(lib().polymul_batch_describe(arr, len(descs), int(order), jobs.ctypes.data, n.value, prods.ctypes.data,
+    _check(lib().polymul_batch_describe(arr, len(descs), int(order), int(full_transforms), None, 0, None,
                                         ctypes.byref(n)), "polymul_batch_describe")
+    jobs = np.zeros((max(1, n.value), 4), dtype=np.uint32)
+    prods = np.zeros((max(1, len(descs)), 4), dtype=np.uint32)
+    _check(lib().polymul_batch_describe(arr, len(descs), int(order), int(full_transforms), jobs.ctypes.data, n.value,
+                                        prods.ctypes.data, ctypes.byref(n)), "polymul_batch_describe")
     return jobs[:n.value], prods[:len(descs)]
 
 

@@ -15,6 +15,7 @@ constexpr int kMaxColLog = 8;      // K1 <= 8: N <= 2^21 in a batch
 constexpr int kMaxRegColLog = 4;   // K1 <= 4: column levels in registers
 constexpr int kWholeMaxLog = 15;   // split products up to 2^15: one CTA runs all their jobs
 constexpr int kMaxPrimes = 8;
+constexpr int kMinTftColLog = 2;   // row-granular TFT for 2 <= K1 <= 4 (register column passes)
 
 enum : uint32_t { JOB_SMALL = 0, JOB_COLF = 1, JOB_ROW = 2, JOB_COLI = 3, JOB_WHOLE = 4 };
 
@@ -22,14 +23,23 @@ struct Job {
     uint32_t type, k, prod, idx;   // idx: tile / row index, or the number of products of a SMALL job
 };
 
+// A split product (N > 2^13) is 2^K1 rows of 2^13 (K1 = log2 N - 13).  With
+// tft set it runs as a truncated transform at row granularity: only the
+// first nrows = ceil(lc / 2^13) < 2^K1 rows (the first nrows x 2^13 outputs
+// of the forward transforms in bit-reversed order) are computed, and the
+// inverse column pass is an inverse TFT of nrows known outputs per column;
+// k_scale is then (2^13)^-1 R^2 (the column pass scales exactly) instead of
+// N^-1 R^2.
 struct Prod {
     const uint32_t *a, *b;
     uint32_t *c;
     uint32_t *ws;         // 2N words, large products only
     uint32_t la, lb, lc, k;
-    uint32_t prime, k_scale;
+    uint16_t prime, tft;
+    uint32_t k_scale;
     uint32_t ntiles, nrows;
 };
+static_assert(sizeof(Prod) == 64, "product table entry");
 
 struct PrimeInfo {
     uint32_t p, pp;
@@ -66,8 +76,10 @@ struct BatchHost {
 // Validates the descriptors and builds the batch.  Products are stored small
 // (N <= 2^13, sorted by size) first, then split ones.  Primes are looked up
 // in prime_list (extended, and prime_log2 raised, unless fixed_primes).
+// With tft, split products with 2 <= K1 <= 4 whose output leaves rows
+// unused run as row-granular truncated transforms.
 int batch_build(const polymul_desc *descs, size_t count, BatchHost &out, std::vector<uint32_t> &prime_list,
-                std::vector<int> &prime_log2, bool fixed_primes);
+                std::vector<int> &prime_log2, bool fixed_primes, bool tft);
 // Replaces scratch offsets by pointers into ws.
 void batch_rebase(BatchHost &b, uint32_t *ws);
 // Opts kernel variant (0: 2 CTAs/SM register budget, 1: 3 CTAs/SM) into its

@@ -46,7 +46,7 @@ int build(const polymul_desc *descs, size_t count, BatchHost &h, std::vector<uin
 {
     if (!descs) return MONT_EINVAL;
     if (count > (size_t{1} << 31)) return MONT_ERANGE;
-    return batch_build(descs, count, h, primes, logs, false);
+    return batch_build(descs, count, h, primes, logs, false, true);
 }
 
 }  // namespace

@@ -37,12 +37,30 @@ __device__ __forceinline__ int brev(int k)
     else return static_cast<int>(__brev(static_cast<unsigned>(k)) >> (32 - LOGN));
 }
 
+// Natural-order I/O of a transform held in the padded layout at bit-reversed
+// positions (word k of the natural order sits at brev(k)).  A warp that
+// walks 32 consecutive k hits brev(k) at addresses whose low bits repeat,
+// 2- to 16-way bank conflicts for N = 2^11 .. 2^14.  Instead, lane-step m
+// covers the S consecutive words k = S m + r, r < S, with
+// S = max(4, 2^(log2 N - 10)), and the lanes of a warp take consecutive m:
+// for a fixed r the 32 lanes then differ in bits 5 .. 9 of brev(k) (bits
+// 4 .. 8 for N = 2^11), which the padding word per 32 maps onto 32 distinct
+// banks.  Each lane moves its S words of global memory as S / 4 uint4.
+template <int LOGN, int NT>
+struct BrevIO {
+    static constexpr int N = 1 << LOGN;
+    static constexpr int S = LOGN > 12 ? (1 << (LOGN - 10)) : 4;
+    static constexpr int STEPS = N / S / NT;
+    static constexpr bool kUse = LOGN >= 11 && STEPS >= 1 && N % (S * NT) == 0;
+};
+
 struct NttArgs {
     uint32_t *data;
     size_t batch;
     const uint32_t *tw;
     uint32_t p, pp, ninv_mont;
     int bitrev;
+    int aligned16;   // data 16-byte aligned: rows move as uint4
 };
 
 // In-place forward NTT of [batch][N]; natural order in, natural (or, with
@@ -79,8 +97,28 @@ k_ntt_fwd(NttArgs A)
         __syncthreads();
         fwd_passes<LOGN, NT, 1, true, 1, NP - 1>(lay, tid, A.tw, 0, 0, md);
     }
-    if (valid)
-        for (int k = tid; k < N; k += NT) g[k] = csub(lay[0][A.bitrev ? k : brev<LOGN>(k)], A.p);
+    if (!valid) return;
+    if constexpr (BrevIO<LOGN, NT>::kUse) {
+        using IO = BrevIO<LOGN, NT>;
+        if (!A.bitrev && A.aligned16) {
+#pragma unroll
+            for (int i = 0; i < IO::STEPS; i++) {
+                const int k0 = IO::S * (tid + NT * i);
+                uint4 *dst = reinterpret_cast<uint4 *>(g + k0);
+#pragma unroll
+                for (int q = 0; q < IO::S / 4; q++) {
+                    uint4 v;
+                    v.x = csub(lay[0][brev<LOGN>(k0 + 4 * q)], A.p);
+                    v.y = csub(lay[0][brev<LOGN>(k0 + 4 * q + 1)], A.p);
+                    v.z = csub(lay[0][brev<LOGN>(k0 + 4 * q + 2)], A.p);
+                    v.w = csub(lay[0][brev<LOGN>(k0 + 4 * q + 3)], A.p);
+                    dst[q] = v;
+                }
+            }
+            return;
+        }
+    }
+    for (int k = tid; k < N; k += NT) g[k] = csub(lay[0][A.bitrev ? k : brev<LOGN>(k)], A.p);
 }
 
 // In-place inverse NTT (with the factor N^-1) of [batch][N]; natural (or,
@@ -98,7 +136,33 @@ k_ntt_inv(NttArgs A)
     const PadLayout lay = {smem + static_cast<size_t>(team) * PadLayout::words(N)};
     const Mod md{A.p, A.pp};
     const int bitrev = A.bitrev;
-    stage_in<N, NT>(lay, g, tid, valid, [bitrev](int k) { return bitrev ? k : brev<LOGN>(k); });
+    bool staged = false;
+    if constexpr (BrevIO<LOGN, NT>::kUse) {
+        using IO = BrevIO<LOGN, NT>;
+        if (!bitrev && A.aligned16) {
+            // every uint4 load of the thread in flight before its first store
+            uint4 v[IO::STEPS][IO::S / 4];
+#pragma unroll
+            for (int i = 0; i < IO::STEPS; i++)
+#pragma unroll
+                for (int q = 0; q < IO::S / 4; q++)
+                    v[i][q] = valid ? reinterpret_cast<const uint4 *>(g + IO::S * (tid + NT * i))[q]
+                                    : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+            for (int i = 0; i < IO::STEPS; i++) {
+                const int k0 = IO::S * (tid + NT * i);
+#pragma unroll
+                for (int q = 0; q < IO::S / 4; q++) {
+                    lay[brev<LOGN>(k0 + 4 * q)] = v[i][q].x;
+                    lay[brev<LOGN>(k0 + 4 * q + 1)] = v[i][q].y;
+                    lay[brev<LOGN>(k0 + 4 * q + 2)] = v[i][q].z;
+                    lay[brev<LOGN>(k0 + 4 * q + 3)] = v[i][q].w;
+                }
+            }
+            staged = true;
+        }
+    }
+    if (!staged) stage_in<N, NT>(lay, g, tid, valid, [bitrev](int k) { return bitrev ? k : brev<LOGN>(k); });
     __syncthreads();
     if constexpr (NP <= 1) {
         inv_passes<LOGN, NT, true, NP - 1, 0>(lay, tid, A.tw, 0, 0, md);
@@ -159,6 +223,7 @@ int ntt_common(const ntt_plan *plan, uint32_t *data, size_t batch, int flags, bo
     A.pp = plan->p_prime;
     A.ninv_mont = plan->ninv_mont;
     A.bitrev = (flags & NTT_BITREV) ? 1 : 0;
+    A.aligned16 = (reinterpret_cast<uintptr_t>(data) & 15u) == 0;
     switch (plan->log2n) {
 #define X(L) \
     case L: return launch_ntt_smem<L>(A, inverse, s);

@@ -252,13 +252,16 @@ __device__ __forceinline__ void col_regs(const Prod &P, const PrimeInfo &pr, uin
 #pragma unroll
                 for (int t = 0; t < N1; t++) x[G + g][t] = mont_mul(x[G + g][t], P.k_scale, pr.p, pr.pp);
             ct_group<K1, NA, true>(x, pr.tw, 0, 0, md);
+            // Row t of the column outputs goes to scratch row t; a truncated
+            // product (tft) computes and reads only its first nrows rows.
 #pragma unroll
             for (int a = 0; a < 2; a++)
 #pragma unroll
                 for (int g = 0; g < G; g++)
 #pragma unroll
                     for (int t = 0; t < N1; t++)
-                        P.ws[a * n + cs + g * kThreads + (static_cast<size_t>(t) << kRowLog)] = x[a * G + g][t];
+                        if (static_cast<uint32_t>(t) < P.nrows)
+                            P.ws[a * n + cs + g * kThreads + (static_cast<size_t>(t) << kRowLog)] = x[a * G + g][t];
         } else {
 #pragma unroll
             for (int g = 0; g < G; g++)
@@ -273,6 +276,112 @@ __device__ __forceinline__ void col_regs(const Prod &P, const PrimeInfo &pr, uin
                     const size_t j = cs + g * kThreads + (static_cast<size_t>(t) << kRowLog);
                     if (j < P.lc) P.c[j] = x[g][t];
                 }
+        }
+    }
+}
+
+// x / 2 mod P for x in [0, P): x >> 1, plus (P + 1) / 2 when x is odd.
+__device__ __forceinline__ uint32_t half_mod(uint32_t x, uint32_t p)
+{
+    return (x >> 1) + ((x & 1u) ? (p >> 1) + 1u : 0u);
+}
+
+// Inverse truncated Fourier transform of one column (van der Hoeven's
+// recursion) over node `block I of level S` of the column transform, SIZE
+// entries at x[OFF ..): on entry x[OFF .. OFF + L) holds the node's outputs
+// (bit-reversed order) and x[OFF + L .. OFF + SIZE) its level-S inputs; on
+// return x[OFF .. OFF + SIZE) holds all of its level-S inputs.  The node's
+// butterfly is (x, y) -> (x + r y, x - r y) with r = tw[2^S + I]:
+//  - L >= SIZE/2: the left child's inputs u follow from its (all known)
+//    outputs; the right child's inputs v_j = u_j - 2 r x_{j+h} are known for
+//    j >= L - h, the rest follow from its L - h outputs; then
+//    x_j = (u_j + v_j) / 2 and x_{j+h} = (u_j - v_j) / (2 r);
+//  - L < SIZE/2: for j >= L the left child's input u_j = x_j + r x_{j+h} is
+//    known, the others follow from its L outputs, then x_j = u_j - r x_{j+h}.
+// All values in [0, P); every division is exact (no deferred scale factor).
+template <int N1, int OFF, int SIZE, int L, int S, int I>
+__device__ __forceinline__ void itft_node(uint32_t (&x)[N1], const uint32_t *__restrict__ tw,
+                                          const uint32_t *__restrict__ itw, Mod m)
+{
+    if constexpr (SIZE > 1 && L > 0) {
+        constexpr int H = SIZE / 2;
+        const uint32_t r = __ldg(tw + (1 << S) + I);   // Montgomery form: REDC(y, r) = y w
+        if constexpr (L >= H) {
+            itft_node<N1, OFF, H, H, S + 1, 2 * I>(x, tw, itw, m);
+            const uint32_t r2 = add_mod(r, r, m.p);
+#pragma unroll
+            for (int j = L - H; j < H; j++)
+                x[OFF + H + j] = sub_mod(x[OFF + j], mont_mul(x[OFF + H + j], r2, m.p, m.pp), m.p);
+            itft_node<N1, OFF + H, H, L - H, S + 1, 2 * I + 1>(x, tw, itw, m);
+            const uint32_t ri = __ldg(itw + (1 << S) + I);
+#pragma unroll
+            for (int j = 0; j < H; j++) {
+                const uint32_t u = x[OFF + j], v = x[OFF + H + j];
+                x[OFF + j] = half_mod(add_mod(u, v, m.p), m.p);
+                x[OFF + H + j] = half_mod(mont_mul(u - v + m.p, ri, m.p, m.pp), m.p);
+            }
+        } else {
+#pragma unroll
+            for (int j = L; j < H; j++) x[OFF + j] = add_mod(x[OFF + j], mont_mul(x[OFF + H + j], r, m.p, m.pp), m.p);
+            itft_node<N1, OFF, H, L, S + 1, 2 * I>(x, tw, itw, m);
+#pragma unroll
+            for (int j = 0; j < H; j++) x[OFF + j] = sub_mod(x[OFF + j], mont_mul(x[OFF + H + j], r, m.p, m.pp), m.p);
+        }
+    }
+}
+
+// Inverse column pass of a truncated split product (K1 <= 4 column levels,
+// L = nrows rows computed): the columns of reg_cols(K1) consecutive columns,
+// each an inverse TFT of its L known outputs (the rows) with its inputs
+// beyond L known to be zero (c is zero from L x 2^13 on), written to c.
+template <int K1, int L>
+__device__ __forceinline__ void col_regs_itft(const Prod &P, const PrimeInfo &pr, uint32_t tile)
+{
+    constexpr int N1 = 1 << K1, G = 16 / N1, STEPS = reg_cols(K1) / kThreads / G;
+    const Mod md{pr.p, pr.pp};
+    const size_t c0 = static_cast<size_t>(tile) * reg_cols(K1) + threadIdx.x;
+#pragma unroll 1
+    for (int st = 0; st < STEPS; st++) {
+        const size_t cs = c0 + static_cast<size_t>(st) * G * kThreads;
+        uint32_t x[G][N1];
+#pragma unroll
+        for (int g = 0; g < G; g++)
+#pragma unroll
+            for (int t = 0; t < N1; t++)
+                x[g][t] = t < L ? P.ws[cs + g * kThreads + (static_cast<size_t>(t) << kRowLog)] : 0u;
+#pragma unroll
+        for (int g = 0; g < G; g++) itft_node<N1, 0, N1, L, 0, 0>(x[g], pr.tw, pr.itw, md);
+#pragma unroll
+        for (int g = 0; g < G; g++)
+#pragma unroll
+            for (int t = 0; t < L; t++) {
+                const size_t j = cs + g * kThreads + (static_cast<size_t>(t) << kRowLog);
+                if (j < P.lc) P.c[j] = x[g][t];
+            }
+    }
+}
+
+template <int K1>
+__device__ __forceinline__ void col_itft_dispatch(const Prod &P, const PrimeInfo &pr, uint32_t tile)
+{
+    // nrows lies in (2^(K1-1), 2^K1): the product is longer than half of N.
+    if constexpr (K1 == 2) {
+        col_regs_itft<2, 3>(P, pr, tile);
+    } else if constexpr (K1 == 3) {
+        switch (P.nrows) {
+        case 5: col_regs_itft<3, 5>(P, pr, tile); break;
+        case 6: col_regs_itft<3, 6>(P, pr, tile); break;
+        default: col_regs_itft<3, 7>(P, pr, tile); break;
+        }
+    } else if constexpr (K1 == 4) {
+        switch (P.nrows) {
+        case 9: col_regs_itft<4, 9>(P, pr, tile); break;
+        case 10: col_regs_itft<4, 10>(P, pr, tile); break;
+        case 11: col_regs_itft<4, 11>(P, pr, tile); break;
+        case 12: col_regs_itft<4, 12>(P, pr, tile); break;
+        case 13: col_regs_itft<4, 13>(P, pr, tile); break;
+        case 14: col_regs_itft<4, 14>(P, pr, tile); break;
+        default: col_regs_itft<4, 15>(P, pr, tile); break;
         }
     }
 }
@@ -343,7 +452,12 @@ __device__ __forceinline__ void whole_job(uint32_t *smem, const Prod &P, const P
                                                            pr.tw, pr.itw, K1, static_cast<int>(r), md);
         __syncthreads();
     }
-    for (uint32_t t = 0; t < P.ntiles; t++) col_regs<K1, true>(P, pr, t);
+    if (P.tft) {
+        if constexpr (K1 >= kMinTftColLog)
+            for (uint32_t t = 0; t < P.ntiles; t++) col_itft_dispatch<K1>(P, pr, t);
+    } else {
+        for (uint32_t t = 0; t < P.ntiles; t++) col_regs<K1, true>(P, pr, t);
+    }
 }
 
 __device__ __forceinline__ void whole_dispatch(uint32_t *smem, const Prod &P, const PrimeInfo &pr)
@@ -359,6 +473,15 @@ __device__ __forceinline__ void whole_dispatch(uint32_t *smem, const Prod &P, co
 template <bool INV>
 __device__ __forceinline__ void col_job(uint32_t *smem, const Prod &P, const PrimeInfo &pr, uint32_t tile)
 {
+    if (INV && P.tft) {
+        switch (P.k - kRowLog) {
+        case 2: col_itft_dispatch<2>(P, pr, tile); break;
+        case 3: col_itft_dispatch<3>(P, pr, tile); break;
+        case 4: col_itft_dispatch<4>(P, pr, tile); break;
+        default: break;
+        }
+        return;
+    }
     switch (P.k - kRowLog) {
     case 1: col_regs<1, INV>(P, pr, tile); break;
     case 2: col_regs<2, INV>(P, pr, tile); break;
@@ -498,7 +621,7 @@ size_t batch_ws_words(size_t lc)
 }
 
 int batch_build(const polymul_desc *descs, size_t count, BatchHost &out, std::vector<uint32_t> &prime_list,
-                std::vector<int> &prime_log2, bool fixed_primes)
+                std::vector<int> &prime_log2, bool fixed_primes, bool tft)
 {
     out.prods.clear();
     for (auto &j : out.jobs) j.clear();
@@ -537,19 +660,28 @@ int batch_build(const polymul_desc *descs, size_t count, BatchHost &out, std::ve
         P.lb = d.lb;
         P.lc = static_cast<uint32_t>(lc);
         P.k = static_cast<uint32_t>(k);
-        P.prime = static_cast<uint32_t>(pi);
-        const uint32_t n_mod = static_cast<uint32_t>((uint64_t{1} << k) % d.p);
-        P.k_scale = host_to_mont(host_to_mont(host_powmod(n_mod, d.p - 2, d.p), d.p), d.p);   // N^-1 R^2
+        P.prime = static_cast<uint16_t>(pi);
+        P.tft = 0;
         P.ntiles = P.nrows = 0;
+        int scale_log = k;   // b is scaled by (2^scale_log)^-1 R^2
         if (k > kSmallLog) {
-            P.ntiles = static_cast<uint32_t>(col_tiles(k - kRowLog));
-            P.nrows = 1u << (k - kRowLog);
+            const int k1 = k - kRowLog;
+            P.ntiles = static_cast<uint32_t>(col_tiles(k1));
+            P.nrows = 1u << k1;
+            const uint32_t need = static_cast<uint32_t>((lc + (size_t{1} << kRowLog) - 1) >> kRowLog);
+            if (tft && k1 >= kMinTftColLog && k1 <= kMaxRegColLog && need < P.nrows) {
+                P.tft = 1;
+                P.nrows = need;
+                scale_log = kRowLog;
+            }
             P.ws = reinterpret_cast<uint32_t *>(out.ws_words);   // word offset until rebased
             out.ws_words += size_t{2} << k;
             large.push_back(i);
         } else {
             small.push_back(i);
         }
+        const uint32_t n_mod = static_cast<uint32_t>((uint64_t{1} << scale_log) % d.p);
+        P.k_scale = host_to_mont(host_to_mont(host_powmod(n_mod, d.p - 2, d.p), d.p), d.p);
     }
     std::stable_sort(small.begin(), small.end(), [&](size_t x, size_t y) { return prods[x].k < prods[y].k; });
     out.prods.reserve(count);
@@ -657,14 +789,18 @@ int batch_launch(BatchArgs A, const Job *jobs, uint32_t njobs, size_t sync_words
 
 }  // namespace mont
 
+// host[v], d_jobs[v], d_prods[v]: the batch with row-granular truncated
+// transforms (v = 0) and with every product padded to a full transform
+// (v = 1, polymul_batch_config.full_transforms); both share counters and
+// scratch (the same layout).
 struct polymul_batch_plan {
     int device = 0;
-    mont::BatchHost host;
+    mont::BatchHost host[2];
     std::vector<uint32_t> prime_list;
     std::vector<int> prime_log2;
     mont::BatchArgs args{};
-    mont::Job *d_jobs[mont::kJobOrders] = {};
-    mont::Prod *d_prods = nullptr;
+    mont::Job *d_jobs[2][mont::kJobOrders] = {};
+    mont::Prod *d_prods[2] = {};
     uint32_t *d_sync = nullptr;
     size_t sync_words = 0;
     uint32_t *d_ws = nullptr;
@@ -686,7 +822,7 @@ std::map<std::string, polymul_batch_config> g_tune_cache;
 std::string signature(const polymul_batch_plan *pl)
 {
     std::map<uint32_t, size_t> hist;
-    for (const Prod &P : pl->host.prods) hist[P.k]++;
+    for (const Prod &P : pl->host[0].prods) hist[P.k]++;
     std::string s = std::to_string(pl->device) + ":";
     for (auto &kv : hist) s += std::to_string(kv.first) + "x" + std::to_string(kv.second) + ",";
     return s;
@@ -696,8 +832,9 @@ void free_plan(polymul_batch_plan *pl)
 {
     if (pl->graph) cudaGraphExecDestroy(pl->graph);
     if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
-    for (mont::Job *j : pl->d_jobs) cudaFree(j);
-    cudaFree(pl->d_prods);
+    for (auto &v : pl->d_jobs)
+        for (mont::Job *j : v) cudaFree(j);
+    for (mont::Prod *d : pl->d_prods) cudaFree(d);
     cudaFree(pl->d_sync);
     cudaFree(pl->d_ws);
 }
@@ -706,25 +843,30 @@ int launch(polymul_batch_plan *pl, const polymul_batch_config &cfg, cudaStream_t
 {
     const int order = (cfg.order >= 0 && cfg.order < kJobOrders) ? cfg.order : 0;
     const int variant = cfg.kernel == 1 ? 1 : 0;
+    const int full = cfg.full_transforms ? 1 : 0;
     const int occ = pl->occ[variant];
     const int per_sm = std::max(1, std::min(cfg.ctas_per_sm > 0 ? cfg.ctas_per_sm : occ, occ));
-    return batch_launch(pl->args, pl->d_jobs[order], static_cast<uint32_t>(pl->host.jobs[order].size()),
+    BatchArgs A = pl->args;
+    A.prods = pl->d_prods[full];
+    return batch_launch(A, pl->d_jobs[full][order], static_cast<uint32_t>(pl->host[full].jobs[order].size()),
                         pl->sync_words, pl->sms * per_sm, variant, s);
 }
 
 }  // namespace
 }  // namespace mont
 
-extern "C" int polymul_batch_describe(const polymul_desc *descs, size_t count, int order, uint32_t *jobs,
-                                      size_t cap, uint32_t *prods, size_t *njobs)
+extern "C" int polymul_batch_describe(const polymul_desc *descs, size_t count, int order, int full_transforms,
+                                      uint32_t *jobs, size_t cap, uint32_t *prods, size_t *njobs)
 {
     using namespace mont;
-    if (!njobs || (count && !descs) || order < 0 || order >= kJobOrders || (cap && !jobs)) return MONT_EINVAL;
+    if (!njobs || (count && !descs) || order < 0 || order >= kJobOrders || (cap && !jobs) ||
+        (full_transforms != 0 && full_transforms != 1))
+        return MONT_EINVAL;
     if (count > (size_t{1} << 31)) return MONT_ERANGE;
     BatchHost host;
     std::vector<uint32_t> prime_list;
     std::vector<int> prime_log2;
-    const int rc = batch_build(descs, count, host, prime_list, prime_log2, false);
+    const int rc = batch_build(descs, count, host, prime_list, prime_log2, false, full_transforms == 0);
     if (rc != MONT_OK) return rc;
     const std::vector<Job> &list = host.jobs[order];
     *njobs = list.size();
@@ -736,9 +878,10 @@ extern "C" int polymul_batch_describe(const polymul_desc *descs, size_t count, i
     }
     if (prods)
         for (size_t i = 0; i < host.prods.size(); i++) {
-            prods[3 * i] = host.prods[i].k;
-            prods[3 * i + 1] = host.prods[i].ntiles;
-            prods[3 * i + 2] = host.prods[i].nrows;
+            prods[4 * i] = host.prods[i].k;
+            prods[4 * i + 1] = host.prods[i].ntiles;
+            prods[4 * i + 2] = host.prods[i].nrows;
+            prods[4 * i + 3] = host.prods[i].tft;
         }
     return MONT_OK;
 }
@@ -752,7 +895,8 @@ extern "C" int polymul_batch_plan_create(const polymul_desc *descs, size_t count
     polymul_batch_plan *pl = new (std::nothrow) polymul_batch_plan();
     if (!pl) return MONT_ENOMEM;
     int rc = cudaGetDevice(&pl->device) == cudaSuccess ? MONT_OK : MONT_ECUDA;
-    if (rc == MONT_OK) rc = batch_build(descs, count, pl->host, pl->prime_list, pl->prime_log2, false);
+    if (rc == MONT_OK) rc = batch_build(descs, count, pl->host[0], pl->prime_list, pl->prime_log2, false, true);
+    if (rc == MONT_OK) rc = batch_build(descs, count, pl->host[1], pl->prime_list, pl->prime_log2, true, false);
     for (size_t pi = 0; pi < pl->prime_list.size() && rc == MONT_OK; pi++) {
         const TwTable *t = nullptr;
         rc = get_table(pl->prime_list[pi], std::max(pl->prime_log2[pi], kRowLog), &t);
@@ -766,17 +910,21 @@ extern "C" int polymul_batch_plan_create(const polymul_desc *descs, size_t count
     pl->sync_words = 2 + 2 * count;
     ok = cudaMalloc(&pl->d_sync, pl->sync_words * sizeof(uint32_t)) == cudaSuccess &&
          cudaMemset(pl->d_sync, 0, pl->sync_words * sizeof(uint32_t)) == cudaSuccess;
-    if (ok && pl->host.ws_words) ok = cudaMalloc(&pl->d_ws, pl->host.ws_words * sizeof(uint32_t)) == cudaSuccess;
-    if (ok) batch_rebase(pl->host, pl->d_ws);
-    if (ok && count)
-        ok = cudaMalloc(&pl->d_prods, count * sizeof(Prod)) == cudaSuccess &&
-             cudaMemcpy(pl->d_prods, pl->host.prods.data(), count * sizeof(Prod), cudaMemcpyHostToDevice) ==
-                 cudaSuccess;
-    for (int o = 0; o < kJobOrders && ok; o++)
-        if (!pl->host.jobs[o].empty())
-            ok = cudaMalloc(&pl->d_jobs[o], pl->host.jobs[o].size() * sizeof(Job)) == cudaSuccess &&
-                 cudaMemcpy(pl->d_jobs[o], pl->host.jobs[o].data(), pl->host.jobs[o].size() * sizeof(Job),
-                            cudaMemcpyHostToDevice) == cudaSuccess;
+    if (ok && pl->host[0].ws_words)
+        ok = cudaMalloc(&pl->d_ws, pl->host[0].ws_words * sizeof(uint32_t)) == cudaSuccess;
+    for (int v = 0; v < 2 && ok; v++) {
+        BatchHost &h = pl->host[v];
+        batch_rebase(h, pl->d_ws);
+        if (count)
+            ok = cudaMalloc(&pl->d_prods[v], count * sizeof(Prod)) == cudaSuccess &&
+                 cudaMemcpy(pl->d_prods[v], h.prods.data(), count * sizeof(Prod), cudaMemcpyHostToDevice) ==
+                     cudaSuccess;
+        for (int o = 0; o < kJobOrders && ok; o++)
+            if (!h.jobs[o].empty())
+                ok = cudaMalloc(&pl->d_jobs[v][o], h.jobs[o].size() * sizeof(Job)) == cudaSuccess &&
+                     cudaMemcpy(pl->d_jobs[v][o], h.jobs[o].data(), h.jobs[o].size() * sizeof(Job),
+                                cudaMemcpyHostToDevice) == cudaSuccess;
+    }
     if (ok) ok = batch_occupancy(0, &pl->occ[0]) == MONT_OK && batch_occupancy(1, &pl->occ[1]) == MONT_OK;
     pl->occupancy = pl->occ[0];
     pl->sms = device_sm_count();
@@ -786,13 +934,14 @@ extern "C" int polymul_batch_plan_create(const polymul_desc *descs, size_t count
         delete pl;
         return MONT_ENOMEM;
     }
-    pl->args.prods = pl->d_prods;
+    pl->args.prods = pl->d_prods[0];
     pl->args.sync = pl->d_sync;
     pl->args.wait_iters = 1u << 22;
     pl->args.wait_ns = 2000000000ull;   // 2 s per wait
     pl->cfg.ctas_per_sm = pl->occ[0];
     pl->cfg.order = 0;
     pl->cfg.kernel = 0;
+    pl->cfg.full_transforms = 0;
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune_cache.find(signature(pl));
@@ -811,7 +960,7 @@ extern "C" void polymul_batch_plan_destroy(polymul_batch_plan *plan)
 
 extern "C" size_t polymul_batch_plan_workspace_bytes(const polymul_batch_plan *plan)
 {
-    return plan ? plan->host.ws_words * sizeof(uint32_t) : 0;
+    return plan ? plan->host[0].ws_words * sizeof(uint32_t) : 0;
 }
 
 extern "C" int polymul_batch_plan_get_config(const polymul_batch_plan *plan, polymul_batch_config *cfg)
@@ -824,7 +973,7 @@ extern "C" int polymul_batch_plan_get_config(const polymul_batch_plan *plan, pol
 extern "C" int polymul_batch_plan_set_config(polymul_batch_plan *plan, const polymul_batch_config *cfg)
 {
     if (!plan || !cfg || cfg->ctas_per_sm < 0 || cfg->order < 0 || cfg->order >= mont::kJobOrders || cfg->kernel < 0 ||
-        cfg->kernel > 1)
+        cfg->kernel > 1 || cfg->full_transforms < 0 || cfg->full_transforms > 1)
         return MONT_EINVAL;
     plan->cfg = *cfg;
     return MONT_OK;
@@ -858,7 +1007,8 @@ extern "C" int polymul_batch_run_graph(polymul_batch_plan *plan, cudaStream_t st
     if (cudaGetDevice(&dev) != cudaSuccess) return MONT_ECUDA;
     if (dev != plan->device) return MONT_EINVAL;
     if (plan->graph && (plan->graph_cfg.ctas_per_sm != plan->cfg.ctas_per_sm || plan->graph_cfg.order != plan->cfg.order ||
-                        plan->graph_cfg.kernel != plan->cfg.kernel)) {
+                        plan->graph_cfg.kernel != plan->cfg.kernel ||
+                        plan->graph_cfg.full_transforms != plan->cfg.full_transforms)) {
         cudaGraphExecDestroy(plan->graph);
         plan->graph = nullptr;
     }
@@ -914,6 +1064,7 @@ extern "C" int polymul_batch_plan_tune(polymul_batch_plan *plan, cudaStream_t st
             c.ctas_per_sm = per;
             c.order = order;
             c.kernel = variant;
+            c.full_transforms = plan->cfg.full_transforms;
             rc = mont::launch(plan, c, stream);   // warm-up
             float total = 0.f;
             for (int t = 0; t < trials && rc == MONT_OK; t++) {
@@ -947,12 +1098,14 @@ extern "C" int polymul_batch_plan_tune(polymul_batch_plan *plan, cudaStream_t st
 extern "C" int polymul_batch_plan_inject_stall(polymul_batch_plan *plan)
 {
     if (!plan) return MONT_EINVAL;
-    for (size_t i = 0; i < plan->host.prods.size(); i++) {
-        mont::Prod &P = plan->host.prods[i];
-        if (P.k <= static_cast<uint32_t>(mont::kWholeMaxLog)) continue;   // no cross-CTA waits
-        P.ntiles += 1;
-        if (cudaMemcpy(plan->d_prods + i, &P, sizeof(mont::Prod), cudaMemcpyHostToDevice) != cudaSuccess)
-            return MONT_ECUDA;
+    for (size_t i = 0; i < plan->host[0].prods.size(); i++) {
+        if (plan->host[0].prods[i].k <= static_cast<uint32_t>(mont::kWholeMaxLog)) continue;   // no cross-CTA waits
+        for (int v = 0; v < 2; v++) {
+            mont::Prod &P = plan->host[v].prods[i];
+            P.ntiles += 1;
+            if (cudaMemcpy(plan->d_prods[v] + i, &P, sizeof(mont::Prod), cudaMemcpyHostToDevice) != cudaSuccess)
+                return MONT_ECUDA;
+        }
         return MONT_OK;
     }
     return MONT_EINVAL;

@@ -305,7 +305,7 @@ int issue_batch(mont_server *sv, Slot &s)
         const Req &q = s.reqs[i];
         descs[i] = polymul_desc{q.da, q.db, q.dc, q.r.la, q.r.lb, q.r.p, 0};
     }
-    int rc = batch_build(descs.data(), descs.size(), s.host, sv->primes, sv->prime_log2, true);
+    int rc = batch_build(descs.data(), descs.size(), s.host, sv->primes, sv->prime_log2, true, true);
     if (rc == MONT_OK) {
         // Each split product uses the scratch of its own request region.
         std::map<const uint32_t *, uint32_t *> ws_of;

@@ -70,7 +70,7 @@ def test_graph_replay_and_tuning_give_identical_results(m):
     assert plan.status() == m.MONT_OK
     assert np.array_equal(to_host(dc)[:wl.c_size], ref)
     cfg = plan.tune(trials=1)
-    assert cfg.ctas_per_sm >= 1 and cfg.order in (0, 1, 2, 3) and cfg.kernel in (0, 1)
+    assert cfg.ctas_per_sm >= 1 and cfg.order in (0, 1, 2, 3) and cfg.kernel in (0, 1) and cfg.full_transforms == 0
     for order, kernel in ((0, 0), (1, 1), (2, 0), (3, 1)):
         c = m.PolymulBatchConfig(1 + kernel, order, kernel)
         plan.config = c
@@ -100,6 +100,57 @@ def test_job_kind_boundaries(m):
         plan.run()
         assert plan.status() == m.MONT_OK
         assert np.array_equal(to_host(dc)[:wl.c_size], oracle_packed(wl)), cfg
+
+
+# Products of N = 2^15 .. 2^17 on both sides of every row boundary of the
+# truncated transforms (rows of 2^13 computed = ceil(lc / 2^13)): one row
+# fewer than the full transform, the last rows count that still saves a
+# row, exact multiples of 2^13, one past them, and asymmetric operands.
+TFT_SHAPES = [(16385, 1), (12289, 12288), (12289, 12289), (8192, 8193), (16385, 16385), (24576, 24577),
+              (28672, 28673), (28673, 28673), (1, 40960), (40961, 1), (32769, 32769), (40000, 40000),
+              (50000, 50000), (61440, 61441), (61441, 61441), (1, 65537), (70000, 1), (100000, 3)]
+
+
+@pytest.mark.parametrize("full", [0, 1])
+def test_truncated_transform_boundaries(m, full):
+    """Split products with and without row-granular truncated transforms
+    (polymul_batch_config.full_transforms), every launch shape family,
+    against the oracle; the descriptors show which products ran truncated."""
+    import torch
+    primes = [synth.PRIMES[i % 3] for i in range(len(TFT_SHAPES))]
+    wl = synth.UnevenBatch(primes, [x for x, _ in TFT_SHAPES], [y for _, y in TFT_SHAPES], (605,))
+    ref = oracle_packed(wl)
+    da, db = to_dev(wl.a), to_dev(wl.b)
+    descs = [m.PolymulDesc(da.data_ptr() + 4 * int(wl.a_off[i]), db.data_ptr() + 4 * int(wl.b_off[i]),
+                           0x10 + 4 * int(wl.c_off[i]), int(wl.la[i]), int(wl.lb[i]), int(wl.primes[i]), 0)
+             for i in range(len(wl))]
+    _, prods = m.polymul_batch_describe(descs, 0, full)
+    assert int(prods[:, 3].sum()) == (0 if full else 14)
+    for cfg in ((0, 0, 1), (1, 0, 0), (3, 2, 1), (2, 3, 0)):
+        dc = torch.full((wl.c_size,), -1, dtype=torch.int32, device="cuda")
+        plan = m.PolymulBatchPlan.from_packed(wl.primes, da, wl.a_off, wl.la, db, wl.b_off, wl.lb, dc, wl.c_off)
+        plan.config = m.PolymulBatchConfig(cfg[0], cfg[1], cfg[2], full)
+        plan.run_graph()
+        assert plan.status() == m.MONT_OK
+        check_all_products(wl, to_host(dc), ref)
+
+
+def test_truncated_equals_full_in_the_mix(m):
+    """The same mixed batch (every size 2^0 .. 2^21) with truncated
+    transforms and with full ones: identical results, equal to the oracle."""
+    wl = mixed_batch(606)
+    ref = oracle_packed(wl)
+    plan, _, _, dc = run_packed(m, wl)
+    assert plan.config.full_transforms == 0
+    got_tft = to_host(dc)[:wl.c_size]
+    c = plan.config
+    c.full_transforms = 1
+    plan.config = c
+    dc.fill_(-1)
+    plan.run()
+    assert plan.status() == m.MONT_OK
+    got_full = to_host(dc)[:wl.c_size]
+    assert np.array_equal(got_tft, ref) and np.array_equal(got_full, ref)
 
 
 def test_alone_equals_in_the_mix(m):
@@ -141,10 +192,11 @@ def test_one_shot_batch_matches_oracle(m):
     assert np.array_equal(got2, oracle_packed(wl2))
 
 
-def check_all_products(wl, got):
+def check_all_products(wl, got, ref=None):
     """Every output word of every product equals the oracle's product (all
     of them, in one OpenMP call of the oracle's radix-2 NTT products)."""
-    ref = oracle_packed(wl)
+    if ref is None:
+        ref = oracle_packed(wl)
     bad = np.flatnonzero(got[:wl.c_size] != ref)
     if bad.size:
         first = int(np.searchsorted(wl.c_off.astype(np.int64), bad[0], side="right") - 1)
@@ -158,12 +210,22 @@ def test_uneven_full_size_exhaustive(m):
     start at 0xFFFFFFFF): every output word of every product against the
     oracle."""
     wl = synth.batch_uneven()
+    ref = oracle_packed(wl)
     plan, _, _, dc = run_packed(m, wl, graph=True, tune=True)
-    check_all_products(wl, to_host(dc))
+    check_all_products(wl, to_host(dc), ref)
     dc.fill_(-1)
     plan.run_graph()
     assert plan.status() == m.MONT_OK
-    check_all_products(wl, to_host(dc))
+    check_all_products(wl, to_host(dc), ref)
+    # the same launch shape with every product padded to its full transform
+    c = plan.config
+    assert c.full_transforms == 0
+    c.full_transforms = 1
+    plan.config = c
+    dc.fill_(-1)
+    plan.run_graph()
+    assert plan.status() == m.MONT_OK
+    check_all_products(wl, to_host(dc), ref)
 
 
 def test_uneven_config_sample(m):

@@ -33,7 +33,16 @@ def fake_descs(m, la, lb, primes):
     return out
 
 
-def check_job_list(jobs, prods):
+def kernel_order_lc(la, lb):
+    """Output lengths in the kernel's product order: products with N <= 2^13
+    first, stably sorted by log2 N, then the others in descriptor order."""
+    lc = [int(x) + int(y) - 1 for x, y in zip(la, lb)]
+    k = [(c - 1).bit_length() for c in lc]
+    small = sorted((i for i in range(len(lc)) if k[i] <= 13), key=lambda i: k[i])
+    return [lc[i] for i in small] + [lc[i] for i in range(len(lc)) if k[i] > 13]
+
+
+def check_job_list(jobs, prods, lc=None):
     count = len(prods)
     small = [0] * count
     whole = [0] * count
@@ -61,23 +70,59 @@ def check_job_list(jobs, prods):
         else:
             raise AssertionError("unknown job kind %d" % kind)
     for q in range(count):
-        k, ntiles, nrows = (int(v) for v in prods[q])
+        k, ntiles, nrows, tft = (int(v) for v in prods[q])
         if k <= 13:
             assert small[q] == 1 and whole[q] == colf[q] == row[q] == coli[q] == 0, q
+            assert tft == 0
         elif k <= 15:
             assert whole[q] == 1 and small[q] == colf[q] == row[q] == coli[q] == 0, q
         else:
             assert (colf[q], row[q], coli[q]) == (ntiles, nrows, ntiles) and small[q] == whole[q] == 0, q
-            assert nrows == 1 << (k - 13)
+        if k > 13:
+            # a truncated product computes just the rows of 2^13 its output
+            # reaches; the others compute all 2^(k - 13)
+            if tft:
+                assert 2 <= k - 13 <= 4 and nrows < 1 << (k - 13)
+            else:
+                assert nrows == 1 << (k - 13)
+    if lc is not None:
+        for q in range(count):
+            k, _, nrows, tft = (int(v) for v in prods[q])
+            if tft:
+                assert (nrows - 1) * 8192 < lc[q] <= nrows * 8192, q
 
 
+@pytest.mark.parametrize("full", [0, 1])
 @pytest.mark.parametrize("order", [0, 1, 2, 3])
-def test_uneven_workload_job_lists(m, order):
-    """The 10,000-product uneven workload (sizes and primes only)."""
+def test_uneven_workload_job_lists(m, order, full):
+    """The 10,000-product uneven workload (sizes and primes only), with
+    truncated transforms (full = 0) and without."""
     lens = synth.loguniform_lengths(10000, 1 << 6, 1 << 16, synth.SEED_BATCH_UNEVEN, 0)
     primes = synth.choose_primes(10000, synth.SEED_BATCH_UNEVEN, 1)
-    jobs, prods = m.polymul_batch_describe(fake_descs(m, lens, lens, primes), order)
+    jobs, prods = m.polymul_batch_describe(fake_descs(m, lens, lens, primes), order, full)
     check_job_list(jobs, prods)
+    tft = prods[:, 3]
+    assert (tft.any() if full == 0 else not tft.any())
+
+
+def test_tft_rows_follow_the_output_length(m):
+    """Products kept in descriptor order among the split ones: rows computed
+    = ceil(lc / 2^13) exactly when that leaves rows of the full transform
+    unused and 2 <= log2 N - 13 <= 4."""
+    la = [16385, 24577, 20000, 40000, 40960, 65536, 32769, 70000, 100000, 131072]
+    lb = [1, 1, 4, 1, 1, 1, 1, 60000, 1, 1]
+    primes = [synth.PRIMES[i % 3] for i in range(len(la))]
+    jobs, prods = m.polymul_batch_describe(fake_descs(m, la, lb, primes), 0, 0)
+    lc = [x + y - 1 for x, y in zip(la, lb)]
+    check_job_list(jobs, prods, lc)
+    got = [(int(p[0]), int(p[2]), int(p[3])) for p in prods]
+    want = []
+    for c in lc:
+        k = (c - 1).bit_length()
+        need = -(-c // 8192)
+        t = int(2 <= k - 13 <= 4 and need < 1 << (k - 13))
+        want.append((k, need if t else 1 << (k - 13), t))
+    assert got == want
 
 
 @pytest.mark.parametrize("order", [0, 1, 2, 3])
@@ -106,8 +151,9 @@ def test_random_batches_job_lists(m, order):
         la = np.exp(rng.uniform(0, np.log(1 << 20), count)).astype(np.int64).clip(1, 1 << 20)
         lb = np.exp(rng.uniform(0, np.log(1 << 20), count)).astype(np.int64).clip(1, 1 << 20)
         primes = [synth.PRIMES[i] for i in rng.integers(0, 3, count)]
-        jobs, prods = m.polymul_batch_describe(fake_descs(m, la, lb, primes), order)
-        check_job_list(jobs, prods)
+        d = fake_descs(m, la, lb, primes)
+        jobs, prods = m.polymul_batch_describe(d, order)
+        check_job_list(jobs, prods, kernel_order_lc(la, lb))
 
 
 def test_describe_rejects_bad_input(m):
@@ -126,7 +172,8 @@ def test_describe_rejects_bad_input(m):
 
 def test_one_shot_workspace_layout(m):
     """polymul_batch's workspace: counters (2 + 2 count words), product table
-    (64 B per product), job list of order 0 (16 B per job), each part rounded
+    (64 B per product), job list of order 0 (16 B per job, truncated
+    transforms on), each part rounded
     up to 256 B, then 2N words of scratch per product with N > 2^13."""
     def up(x):
         return (x + 255) // 256 * 256
@@ -142,3 +189,19 @@ def test_one_shot_workspace_layout(m):
             scratch += 2 * n
     want = up(4 * (2 + 2 * len(descs))) + up(64 * len(descs)) + up(16 * len(jobs)) + 4 * scratch
     assert m.polymul_batch_workspace_bytes(descs) == want
+
+
+def test_bench_row_rule_matches_the_builder(m):
+    """The bench's work and byte counts of truncated products use the same
+    rows-computed rule as the batch builder (compared on the uneven
+    workload's sizes)."""
+    import bench_polymul as bp
+    lens = synth.loguniform_lengths(10000, 1 << 6, 1 << 16, synth.SEED_BATCH_UNEVEN, 0)
+    primes = synth.choose_primes(10000, synth.SEED_BATCH_UNEVEN, 1)
+    _, prods = m.polymul_batch_describe(fake_descs(m, lens, lens, primes), 0, 0)
+    lc = kernel_order_lc(lens, lens)
+    for (k, _, nrows, tft), c in zip(prods.tolist(), lc):
+        rows = bp.tft_rows(1 << k, c)
+        assert (rows is not None) == bool(tft)
+        if tft:
+            assert rows == nrows

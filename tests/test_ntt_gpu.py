@@ -62,6 +62,27 @@ def test_ntt_forward_inverse(m, p, logn):
     assert np.array_equal(to_host(d).reshape(batch, n), oracle_rows(p, x, inverse=True))
 
 
+@pytest.mark.parametrize("logn", [11, 12, 13, 14])
+@pytest.mark.parametrize("offset", [0, 1, 3])
+def test_ntt_natural_order_rows_aligned_and_not(m, logn, offset):
+    """Natural-order transforms of several rows whose data start 16-byte
+    aligned (rows move as uint4, bank-conflict-free bit-reversed positions)
+    or 4 / 12 bytes past it (one word at a time)."""
+    import torch
+    p = synth.P3
+    n, batch = 1 << logn, 3
+    x = synth.residues(batch * n, p, 302, logn, offset).reshape(batch, n)
+    plan = m.ntt_plan_create(p, logn)
+    buf = torch.zeros(batch * n + 4, dtype=torch.int32, device="cuda")
+    d = buf[offset:offset + batch * n]
+    d.copy_(to_dev(x.ravel()))
+    m.ntt_fwd(plan, d)
+    assert np.array_equal(to_host(d).reshape(batch, n), oracle_rows(p, x))
+    m.ntt_inv(plan, d)
+    assert np.array_equal(to_host(d).reshape(batch, n), x)
+    assert not to_host(buf[:offset]).any() and not to_host(buf[offset + batch * n:]).any()
+
+
 @pytest.mark.parametrize("p", synth.PRIMES)
 @pytest.mark.parametrize("la,lb", [(1, 1), (1, 2), (2, 1), (3, 5), (16, 16), (17, 9), (100, 29), (255, 257),
                                    (1024, 1024), (1, 4096), (2048, 2048), (3000, 1000), (5000, 3193),
