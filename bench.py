@@ -162,6 +162,46 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def host_link(torch, h_in, d_in, h_out, d_out, reps=3):
+    """Copy-engine rates between pinned host memory and the device (GB/s):
+    one stream each way alone, then both at once, timed with CUDA events."""
+    nbytes = h_in.numel() * h_in.element_size()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def rate(fn, total):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return total * reps / (e0.elapsed_time(e1) / 1e3) / 1e9
+
+    def h2d():
+        with torch.cuda.stream(s1):
+            d_in.copy_(h_in, non_blocking=True)
+        torch.cuda.current_stream().wait_stream(s1)
+
+    def d2h():
+        with torch.cuda.stream(s2):
+            h_out.copy_(d_out, non_blocking=True)
+        torch.cuda.current_stream().wait_stream(s2)
+
+    def both():
+        with torch.cuda.stream(s1):
+            d_in.copy_(h_in, non_blocking=True)
+        with torch.cuda.stream(s2):
+            h_out.copy_(d_out, non_blocking=True)
+        torch.cuda.current_stream().wait_stream(s1)
+        torch.cuda.current_stream().wait_stream(s2)
+
+    return {"h2d_gbs": rate(h2d, nbytes), "d2h_gbs": rate(d2h, nbytes), "both_total_gbs": rate(both, 2 * nbytes),
+            "bytes_per_copy": nbytes,
+            "method": "cudaMemcpyAsync (torch copy_) of a pinned host buffer, CUDA events"}
+
+
 def run_section(extra, errors, key, fn):
     """Runs one secondary section into extra[key].  A failure (a parity spot
     check, a device error) is recorded in errors[key] and its traceback
@@ -339,11 +379,19 @@ def run_gpu(args, ws, rank, local):
         torch.cuda.synchronize()
         barrier()
         e2e_s = max_over_ranks(time.perf_counter() - w0, dist, "cuda")
+        h2d_bytes, d2h_bytes = len(dev) * (8 + 12) * n, len(dev) * (4 + 4) * n
         e2e = {"value": args.e2e_steps * len(dev) * len(OPS) * n * ws / e2e_s / 1e9, "unit": UNIT,
-               "h2d_bytes_per_step": len(dev) * (8 + 12) * n, "d2h_bytes_per_step": len(dev) * (4 + 4) * n,
+               "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": d2h_bytes,
                "steps": args.e2e_steps,
                "path": "C-ABI mont_mul/mont_fma on pinned host buffers: kernels read operands from and write "
                        "results to host memory over NVLink-C2C, one stream, no staging copies"}
+        link = host_link(torch, host[0][0][0], dev[0][1][0], host[0][1][0], dev[0][2])
+        # Ceiling of the step: its host reads at the measured host-to-device
+        # rate (the writes, at the device-to-host rate, run beside them).
+        t_min = max(h2d_bytes / (link["h2d_gbs"] * 1e9), d2h_bytes / (link["d2h_gbs"] * 1e9))
+        link["step_ceiling"] = len(dev) * len(OPS) * n / t_min / 1e9
+        link["frac_of_ceiling"] = e2e["value"] / ws / link["step_ceiling"]
+        e2e["host_link"] = link
         del host
 
     cpu = None
