@@ -543,10 +543,14 @@ def uneven_batch(m, torch, peaks, steps=10, warmup=3, cpu=True, per_product=True
             hbm += batch_hbm_bytes(n, int(la), int(lb), rows)
         return ops, hbm, counts
 
+    # The persistent kernel (kernel 0, 1) or the phased form (kernel 2: one
+    # kernel per job kind, their traffic recorded together per batch).
+    kern = "batch_phased" if cfg.kernel == 2 else "k_polymul_batch"
+
     def figures(t_ms, truncated):
         ops, hbm, counts = work(truncated)
         return {"ms": t_ms, "value": coeffs / t_ms / 1e6, "unit": "Gcoef/s",
-                "roofline": int_roofline("k_polymul_batch", ops, counts, t_ms, peaks,
+                "roofline": int_roofline(kern, ops, counts, t_ms, peaks,
                                          traffic_units=len(wl) if truncated else None),
                 "hbm_at_pass_count": {"bytes": hbm, "achieved_gbs": hbm / (t_ms / 1e3) / 1e9,
                                       "peak_gbs": peaks["hbm_gbs"],
@@ -558,7 +562,9 @@ def uneven_batch(m, torch, peaks, steps=10, warmup=3, cpu=True, per_product=True
     res = {"workload": "10,000 products, L log-uniform in [2^6, 2^16], primes uniform from "
                        "{2013265921, 469762049, 754974721}, N padded to powers of two",
            "value": tft["value"], "unit": "Gcoef/s", "ms": ms, "steps": steps, "warmup": warmup,
-           "launch": "one persistent kernel per batch, replayed from a CUDA graph",
+           "launch": ("phased form: one kernel per job kind (small products by size, whole products, forward "
+                      "columns, rows, output columns) on three branches of one CUDA graph"
+                      if cfg.kernel == 2 else "one persistent kernel per batch, replayed from a CUDA graph"),
            "tuned_config": {"ctas_per_sm": cfg.ctas_per_sm, "order": cfg.order, "kernel": cfg.kernel,
                             "full_transforms": cfg.full_transforms, "tuned": config is None}, "tune_s": tune_s,
            "workspace_bytes": plan.workspace_bytes(), "l2": "operands + scratch (2.4 GB) larger than L2",

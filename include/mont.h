@@ -253,7 +253,13 @@ typedef struct polymul_desc {
  * 2^(K-13) rows of 2^13, computes only the first ceil((la + lb - 1) / 2^13)
  * rows of the forward transforms (the first outputs in bit-reversed order)
  * and recovers c from them by an inverse TFT over each column; the results
- * are the same, bit for bit.  Products up to 2^13 run
+ * are the same, bit for bit.
+ * Kernel forms: the persistent kernel (0, 1) claims jobs from one list and
+ * waits, bounded, on per-product counters; the phased form (2) runs each job
+ * kind as its own kernel with its own register budget, one CTA per job, in
+ * stream order on `stream` plus two side streams the plan owns (small and
+ * whole products), joined back before the call's work ends: no device-side
+ * waits, and the same results.  Products up to 2^13 run
  * whole in one CTA, products of 2^14 and 2^15 as one whole-product job each,
  * larger ones as column-tile, row and output-tile jobs.  Orders: 0: column
  * tiles first, then whole-product and small jobs, then rows and output
@@ -263,7 +269,8 @@ typedef struct polymul_desc {
 typedef struct polymul_batch_config {
     int ctas_per_sm;
     int order;
-    int kernel;            /* 0: registers budgeted for 2 CTAs per SM; 1: for 3 CTAs per SM */
+    int kernel;            /* 0: persistent kernel, registers budgeted for 2 CTAs per SM; 1: for 3;
+                              2: phased form, one kernel per job kind (ctas_per_sm and order unused) */
     int full_transforms;   /* 0 (default): products of N = 2^15 .. 2^17 whose length leaves rows of
                               2^13 unused run as truncated transforms (below); 1: every product is
                               padded to its full power-of-two transform */

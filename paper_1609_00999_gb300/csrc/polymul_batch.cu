@@ -601,6 +601,102 @@ __global__ void __launch_bounds__(kThreads, MINB) k_polymul_batch(BatchArgs A)
     }
 }
 
+// ---------------------------------------------------------------- phased form
+//
+// The same jobs as separate kernels, one CTA per job (or per team of small
+// products), ordered by stream dependencies instead of device-side waits:
+// every kernel gets the register budget of its own job kind.  A batch runs
+// as: small products (one kernel per size, N <= 2^13) and whole products
+// (2^14, 2^15) on side branches, and the split products' forward column
+// tiles, then their rows, then their output tiles on the main branch; the
+// host joins the branches (polymul_batch_run / the graph of
+// polymul_batch_run_graph).  No kernel waits on another's progress.
+
+// Products prods[first .. first + count), all of size 2^K (K <= 13), one
+// team each, teams_of<K>() per CTA.
+template <int K>
+__global__ void __launch_bounds__(teams_of<K>() * nt_of<K>(), min_ctas_of<K>())
+k_phase_small(BatchArgs A, uint32_t first, uint32_t count)
+{
+    constexpr int NT = nt_of<K>(), TEAMS = teams_of<K>();
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int team = threadIdx.x / NT, tid = threadIdx.x - team * NT;
+    const uint32_t i = blockIdx.x * TEAMS + team;
+    const bool valid = i < count;
+    const Prod &P = A.prods[first + (valid ? i : 0)];
+    const PrimeInfo &pr = A.primes[P.prime];
+    polymul_team<K, true, true, NT>(smem + team * team_smem_words<K>(), tid, P.a, valid ? P.la : 0, P.b,
+                                    valid ? P.lb : 0, P.c, valid ? P.lc : 0, pr.tw, pr.itw, 0, 0, pr.p, pr.pp,
+                                    P.k_scale);
+}
+
+// Whole-product jobs (2^14, 2^15), one CTA each: A.jobs lists them.
+__global__ void __launch_bounds__(kThreads, 3) k_phase_whole(BatchArgs A)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    const Prod &P = A.prods[A.jobs[blockIdx.x].prod];
+    whole_dispatch(smem, P, A.primes[P.prime]);
+}
+
+// Row jobs of split products, one CTA each (their column tiles are done).
+__global__ void __launch_bounds__(kThreads, 3) k_phase_row(BatchArgs A)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    const Job J = A.jobs[blockIdx.x];
+    const Prod &P = A.prods[J.prod];
+    const PrimeInfo &pr = A.primes[P.prime];
+    uint32_t *row = P.ws + (static_cast<size_t>(J.idx) << kRowLog);
+    const size_t n = size_t{1} << P.k;
+    polymul_team<kRowLog, false, false, kThreads>(smem, threadIdx.x, row, size_t{1} << kRowLog, row + n,
+                                                  size_t{1} << kRowLog, row, size_t{1} << kRowLog, pr.tw, pr.itw,
+                                                  static_cast<int>(P.k) - kRowLog, static_cast<int>(J.idx), pr.p,
+                                                  pr.pp, 0u);
+}
+
+// Column jobs with K1 <= 4 column levels (registers, no shared memory):
+// forward (INV false) or inverse, the inverse of a truncated product as an
+// inverse TFT per column.
+template <bool INV>
+__global__ void __launch_bounds__(kThreads, 4) k_phase_col_regs(BatchArgs A)
+{
+    const Job J = A.jobs[blockIdx.x];
+    const Prod &P = A.prods[J.prod];
+    const PrimeInfo &pr = A.primes[P.prime];
+    if (INV && P.tft) {
+        switch (P.k - kRowLog) {
+        case 2: col_itft_dispatch<2>(P, pr, J.idx); break;
+        case 3: col_itft_dispatch<3>(P, pr, J.idx); break;
+        case 4: col_itft_dispatch<4>(P, pr, J.idx); break;
+        default: break;
+        }
+        return;
+    }
+    switch (P.k - kRowLog) {
+    case 1: col_regs<1, INV>(P, pr, J.idx); break;
+    case 2: col_regs<2, INV>(P, pr, J.idx); break;
+    case 3: col_regs<3, INV>(P, pr, J.idx); break;
+    case 4: col_regs<4, INV>(P, pr, J.idx); break;
+    default: break;
+    }
+}
+
+// Column jobs with K1 >= 5 (shared-memory column tiles).
+template <bool INV>
+__global__ void __launch_bounds__(kThreads, 3) k_phase_col_tile(BatchArgs A)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    const Job J = A.jobs[blockIdx.x];
+    const Prod &P = A.prods[J.prod];
+    const PrimeInfo &pr = A.primes[P.prime];
+    switch (P.k - kRowLog) {
+    case 5: col_tile<5, INV>(smem, P, pr, J.idx); break;
+    case 6: col_tile<6, INV>(smem, P, pr, J.idx); break;
+    case 7: col_tile<7, INV>(smem, P, pr, J.idx); break;
+    case 8: col_tile<8, INV>(smem, P, pr, J.idx); break;
+    default: break;
+    }
+}
+
 int col_tiles(int k1)
 {
     return (1 << kRowLog) / (k1 <= kMaxRegColLog ? reg_cols(k1) : col_tile_cols(k1));
@@ -774,6 +870,104 @@ int batch_occupancy(int variant, int *per_sm)
     return *per_sm > 0 ? MONT_OK : MONT_ECUDA;
 }
 
+// Jobs of one batch split by the phased form's kernels.
+enum PhaseList { PH_WHOLE = 0, PH_COLF_REG, PH_COLF_TILE, PH_ROW, PH_COLI_REG, PH_COLI_TILE, PH_LISTS };
+
+struct PhasedHost {
+    std::vector<Job> jobs;            // the lists back to back
+    uint32_t off[PH_LISTS] = {}, cnt[PH_LISTS] = {};
+    std::vector<uint32_t> small;      // (log2 N, first product, count) per size present
+};
+
+void phased_build(const BatchHost &b, PhasedHost &out)
+{
+    std::vector<Job> lists[PH_LISTS];
+    for (const Job &J : b.jobs[0]) {
+        const bool reg = J.k - kRowLog <= static_cast<uint32_t>(kMaxRegColLog);
+        switch (J.type) {
+        case JOB_WHOLE: lists[PH_WHOLE].push_back(J); break;
+        case JOB_COLF: lists[reg ? PH_COLF_REG : PH_COLF_TILE].push_back(J); break;
+        case JOB_ROW: lists[PH_ROW].push_back(J); break;
+        case JOB_COLI: lists[reg ? PH_COLI_REG : PH_COLI_TILE].push_back(J); break;
+        default: break;
+        }
+    }
+    out.jobs.clear();
+    for (int l = 0; l < PH_LISTS; l++) {
+        out.off[l] = static_cast<uint32_t>(out.jobs.size());
+        out.cnt[l] = static_cast<uint32_t>(lists[l].size());
+        out.jobs.insert(out.jobs.end(), lists[l].begin(), lists[l].end());
+    }
+    out.small.clear();
+    for (size_t i = 0; i < b.prods.size() && b.prods[i].k <= static_cast<uint32_t>(kSmallLog);) {
+        size_t e = i;
+        while (e < b.prods.size() && b.prods[e].k == b.prods[i].k) e++;
+        out.small.insert(out.small.end(), {b.prods[i].k, static_cast<uint32_t>(i), static_cast<uint32_t>(e - i)});
+        i = e;
+    }
+}
+
+namespace {
+
+template <int K>
+int launch_phase_small(const BatchArgs &A, uint32_t first, uint32_t count, cudaStream_t s)
+{
+    constexpr int T = teams_of<K>(), NT = nt_of<K>();
+    const size_t smem = static_cast<size_t>(T) * team_smem_words<K>() * sizeof(uint32_t);
+    if (ensure_smem(k_phase_small<K>, smem) != MONT_OK) return MONT_ECUDA;
+    k_phase_small<K><<<(count + T - 1) / T, T * NT, smem, s>>>(A, first, count);
+    return launch_status();
+}
+
+int phase_small(int k, const BatchArgs &A, uint32_t first, uint32_t count, cudaStream_t s)
+{
+    switch (k) {
+#define X(L) \
+    case L: return launch_phase_small<L>(A, first, count, s);
+        X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13)
+#undef X
+    default: return MONT_EUNSUPPORTED;
+    }
+}
+
+template <typename K>
+int phase_jobs(K kernel, BatchArgs A, const Job *jobs, uint32_t count, size_t smem, cudaStream_t s)
+{
+    if (count == 0) return MONT_OK;
+    if (ensure_smem(kernel, smem) != MONT_OK) return MONT_ECUDA;
+    A.jobs = jobs;
+    A.njobs = count;
+    kernel<<<count, kThreads, smem, s>>>(A);
+    return launch_status();
+}
+
+}  // namespace
+
+int batch_launch_phased(BatchArgs A, const PhasedHost &ph, const Job *d_jobs, size_t sync_words, cudaStream_t s,
+                        cudaStream_t aux0, cudaStream_t aux1, cudaEvent_t fork, cudaEvent_t join0, cudaEvent_t join1)
+{
+    if (cudaMemsetAsync(A.sync, 0, sync_words * sizeof(uint32_t), s) != cudaSuccess) return MONT_ECUDA;
+    if (cudaEventRecord(fork, s) != cudaSuccess || cudaStreamWaitEvent(aux0, fork, 0) != cudaSuccess ||
+        cudaStreamWaitEvent(aux1, fork, 0) != cudaSuccess)
+        return MONT_ECUDA;
+    int rc = MONT_OK;
+    for (size_t i = 0; i + 2 < ph.small.size() && rc == MONT_OK; i += 3)
+        rc = phase_small(static_cast<int>(ph.small[i]), A, ph.small[i + 1], ph.small[i + 2], aux0);
+    const size_t smem = kSmemWords * sizeof(uint32_t);
+    auto list = [&](int l) { return d_jobs + ph.off[l]; };
+    if (rc == MONT_OK) rc = phase_jobs(k_phase_whole, A, list(PH_WHOLE), ph.cnt[PH_WHOLE], smem, aux1);
+    if (rc == MONT_OK) rc = phase_jobs(k_phase_col_regs<false>, A, list(PH_COLF_REG), ph.cnt[PH_COLF_REG], 0, s);
+    if (rc == MONT_OK) rc = phase_jobs(k_phase_col_tile<false>, A, list(PH_COLF_TILE), ph.cnt[PH_COLF_TILE], smem, s);
+    if (rc == MONT_OK) rc = phase_jobs(k_phase_row, A, list(PH_ROW), ph.cnt[PH_ROW], smem, s);
+    if (rc == MONT_OK) rc = phase_jobs(k_phase_col_regs<true>, A, list(PH_COLI_REG), ph.cnt[PH_COLI_REG], 0, s);
+    if (rc == MONT_OK) rc = phase_jobs(k_phase_col_tile<true>, A, list(PH_COLI_TILE), ph.cnt[PH_COLI_TILE], smem, s);
+    // Join the side branches back into s (also after a failed launch, so no
+    // branch is left open in a capture).
+    const bool joined = cudaEventRecord(join0, aux0) == cudaSuccess && cudaEventRecord(join1, aux1) == cudaSuccess &&
+                        cudaStreamWaitEvent(s, join0, 0) == cudaSuccess && cudaStreamWaitEvent(s, join1, 0) == cudaSuccess;
+    return rc != MONT_OK ? rc : (joined ? MONT_OK : MONT_ECUDA);
+}
+
 int batch_launch(BatchArgs A, const Job *jobs, uint32_t njobs, size_t sync_words, int grid, int variant,
                  cudaStream_t s)
 {
@@ -801,6 +995,10 @@ struct polymul_batch_plan {
     mont::BatchArgs args{};
     mont::Job *d_jobs[2][mont::kJobOrders] = {};
     mont::Prod *d_prods[2] = {};
+    mont::PhasedHost phased[2];              // the phased form's job lists (kernel 2)
+    mont::Job *d_phased[2] = {};
+    cudaStream_t aux[2] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[2] = {};
     uint32_t *d_sync = nullptr;
     size_t sync_words = 0;
     uint32_t *d_ws = nullptr;
@@ -835,6 +1033,12 @@ void free_plan(polymul_batch_plan *pl)
     for (auto &v : pl->d_jobs)
         for (mont::Job *j : v) cudaFree(j);
     for (mont::Prod *d : pl->d_prods) cudaFree(d);
+    for (mont::Job *j : pl->d_phased) cudaFree(j);
+    for (cudaStream_t a : pl->aux)
+        if (a) cudaStreamDestroy(a);
+    if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
+    for (cudaEvent_t e : pl->ev_join)
+        if (e) cudaEventDestroy(e);
     cudaFree(pl->d_sync);
     cudaFree(pl->d_ws);
 }
@@ -844,6 +1048,12 @@ int launch(polymul_batch_plan *pl, const polymul_batch_config &cfg, cudaStream_t
     const int order = (cfg.order >= 0 && cfg.order < kJobOrders) ? cfg.order : 0;
     const int variant = cfg.kernel == 1 ? 1 : 0;
     const int full = cfg.full_transforms ? 1 : 0;
+    if (cfg.kernel == 2) {
+        BatchArgs A = pl->args;
+        A.prods = pl->d_prods[full];
+        return batch_launch_phased(A, pl->phased[full], pl->d_phased[full], pl->sync_words, s, pl->aux[0], pl->aux[1],
+                                   pl->ev_fork, pl->ev_join[0], pl->ev_join[1]);
+    }
     const int occ = pl->occ[variant];
     const int per_sm = std::max(1, std::min(cfg.ctas_per_sm > 0 ? cfg.ctas_per_sm : occ, occ));
     BatchArgs A = pl->args;
@@ -915,6 +1125,11 @@ extern "C" int polymul_batch_plan_create(const polymul_desc *descs, size_t count
     for (int v = 0; v < 2 && ok; v++) {
         BatchHost &h = pl->host[v];
         batch_rebase(h, pl->d_ws);
+        phased_build(h, pl->phased[v]);
+        const std::vector<Job> &pj = pl->phased[v].jobs;
+        if (!pj.empty())
+            ok = cudaMalloc(&pl->d_phased[v], pj.size() * sizeof(Job)) == cudaSuccess &&
+                 cudaMemcpy(pl->d_phased[v], pj.data(), pj.size() * sizeof(Job), cudaMemcpyHostToDevice) == cudaSuccess;
         if (count)
             ok = cudaMalloc(&pl->d_prods[v], count * sizeof(Prod)) == cudaSuccess &&
                  cudaMemcpy(pl->d_prods[v], h.prods.data(), count * sizeof(Prod), cudaMemcpyHostToDevice) ==
@@ -926,6 +1141,10 @@ extern "C" int polymul_batch_plan_create(const polymul_desc *descs, size_t count
                                 cudaMemcpyHostToDevice) == cudaSuccess;
     }
     if (ok) ok = batch_occupancy(0, &pl->occ[0]) == MONT_OK && batch_occupancy(1, &pl->occ[1]) == MONT_OK;
+    for (int i = 0; i < 2 && ok; i++)
+        ok = cudaStreamCreateWithFlags(&pl->aux[i], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&pl->ev_join[i], cudaEventDisableTiming) == cudaSuccess;
+    if (ok) ok = cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming) == cudaSuccess;
     pl->occupancy = pl->occ[0];
     pl->sms = device_sm_count();
     if (!ok || pl->sms <= 0) {
@@ -973,7 +1192,7 @@ extern "C" int polymul_batch_plan_get_config(const polymul_batch_plan *plan, pol
 extern "C" int polymul_batch_plan_set_config(polymul_batch_plan *plan, const polymul_batch_config *cfg)
 {
     if (!plan || !cfg || cfg->ctas_per_sm < 0 || cfg->order < 0 || cfg->order >= mont::kJobOrders || cfg->kernel < 0 ||
-        cfg->kernel > 1 || cfg->full_transforms < 0 || cfg->full_transforms > 1)
+        cfg->kernel > 2 || cfg->full_transforms < 0 || cfg->full_transforms > 1)
         return MONT_EINVAL;
     plan->cfg = *cfg;
     return MONT_OK;
@@ -1081,6 +1300,28 @@ extern "C" int polymul_batch_plan_tune(polymul_batch_plan *plan, cudaStream_t st
                 best = c;
             }
         }
+    if (rc == MONT_OK) {   // the phased form: launch shape and job order do not apply
+        polymul_batch_config c{};
+        c.ctas_per_sm = 0;
+        c.order = 0;
+        c.kernel = 2;
+        c.full_transforms = plan->cfg.full_transforms;
+        rc = mont::launch(plan, c, stream);
+        float total = 0.f;
+        for (int t = 0; t < trials && rc == MONT_OK; t++) {
+            cudaEventRecord(e0, stream);
+            rc = mont::launch(plan, c, stream);
+            cudaEventRecord(e1, stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) rc = MONT_ECUDA;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            total += ms;
+        }
+        if (rc == MONT_OK && total < best_ms) {
+            best_ms = total;
+            best = c;
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != MONT_OK) return rc;

@@ -70,8 +70,9 @@ def test_graph_replay_and_tuning_give_identical_results(m):
     assert plan.status() == m.MONT_OK
     assert np.array_equal(to_host(dc)[:wl.c_size], ref)
     cfg = plan.tune(trials=1)
-    assert cfg.ctas_per_sm >= 1 and cfg.order in (0, 1, 2, 3) and cfg.kernel in (0, 1) and cfg.full_transforms == 0
-    for order, kernel in ((0, 0), (1, 1), (2, 0), (3, 1)):
+    assert cfg.order in (0, 1, 2, 3) and cfg.kernel in (0, 1, 2) and cfg.full_transforms == 0
+    assert cfg.ctas_per_sm >= 1 or cfg.kernel == 2
+    for order, kernel in ((0, 0), (1, 1), (2, 0), (3, 1), (0, 2)):
         c = m.PolymulBatchConfig(1 + kernel, order, kernel)
         plan.config = c
         dc.fill_(-1)
@@ -90,7 +91,7 @@ def test_job_kind_boundaries(m):
               (65536, 65537), (70000, 1)]
     primes = [synth.PRIMES[i % 3] for i in range(len(shapes))]
     wl = synth.UnevenBatch(primes, [x for x, _ in shapes], [y for _, y in shapes], (604,))
-    for cfg in (None, (1, 0, 0), (3, 2, 1)):
+    for cfg in (None, (1, 0, 0), (3, 2, 1), (0, 0, 2)):
         import torch
         da, db = to_dev(wl.a), to_dev(wl.b)
         dc = torch.full((wl.c_size,), -1, dtype=torch.int32, device="cuda")
@@ -126,7 +127,7 @@ def test_truncated_transform_boundaries(m, full):
              for i in range(len(wl))]
     _, prods = m.polymul_batch_describe(descs, 0, full)
     assert int(prods[:, 3].sum()) == (0 if full else 14)
-    for cfg in ((0, 0, 1), (1, 0, 0), (3, 2, 1), (2, 3, 0)):
+    for cfg in ((0, 0, 1), (1, 0, 0), (3, 2, 1), (2, 3, 0), (0, 0, 2)):
         dc = torch.full((wl.c_size,), -1, dtype=torch.int32, device="cuda")
         plan = m.PolymulBatchPlan.from_packed(wl.primes, da, wl.a_off, wl.la, db, wl.b_off, wl.lb, dc, wl.c_off)
         plan.config = m.PolymulBatchConfig(cfg[0], cfg[1], cfg[2], full)
@@ -137,20 +138,24 @@ def test_truncated_transform_boundaries(m, full):
 
 def test_truncated_equals_full_in_the_mix(m):
     """The same mixed batch (every size 2^0 .. 2^21) with truncated
-    transforms and with full ones: identical results, equal to the oracle."""
+    transforms and with full ones, by the persistent kernel and by the
+    phased form (one kernel per job kind, column tiles up to K1 = 8):
+    identical results, equal to the oracle."""
     wl = mixed_batch(606)
     ref = oracle_packed(wl)
     plan, _, _, dc = run_packed(m, wl)
     assert plan.config.full_transforms == 0
-    got_tft = to_host(dc)[:wl.c_size]
-    c = plan.config
-    c.full_transforms = 1
-    plan.config = c
+    assert np.array_equal(to_host(dc)[:wl.c_size], ref)
+    for kernel, full in ((0, 1), (2, 0), (2, 1)):
+        plan.config = m.PolymulBatchConfig(2, 0, kernel, full)
+        dc.fill_(-1)
+        plan.run()
+        assert plan.status() == m.MONT_OK
+        assert np.array_equal(to_host(dc)[:wl.c_size], ref), (kernel, full)
     dc.fill_(-1)
-    plan.run()
+    plan.run_graph()                                    # the phased form captured in a graph
     assert plan.status() == m.MONT_OK
-    got_full = to_host(dc)[:wl.c_size]
-    assert np.array_equal(got_tft, ref) and np.array_equal(got_full, ref)
+    assert np.array_equal(to_host(dc)[:wl.c_size], ref)
 
 
 def test_alone_equals_in_the_mix(m):
@@ -217,15 +222,17 @@ def test_uneven_full_size_exhaustive(m):
     plan.run_graph()
     assert plan.status() == m.MONT_OK
     check_all_products(wl, to_host(dc), ref)
-    # the same launch shape with every product padded to its full transform
+    # the same launch shape with every product padded to its full transform,
+    # and both transform forms by the other kernel form
     c = plan.config
     assert c.full_transforms == 0
-    c.full_transforms = 1
-    plan.config = c
-    dc.fill_(-1)
-    plan.run_graph()
-    assert plan.status() == m.MONT_OK
-    check_all_products(wl, to_host(dc), ref)
+    other = 0 if c.kernel == 2 else 2
+    for kernel, full in ((c.kernel, 1), (other, 0), (other, 1)):
+        plan.config = m.PolymulBatchConfig(c.ctas_per_sm if kernel != 2 else 0, c.order, kernel, full)
+        dc.fill_(-1)
+        plan.run_graph()
+        assert plan.status() == m.MONT_OK
+        check_all_products(wl, to_host(dc), ref)
 
 
 def test_uneven_config_sample(m):
