@@ -140,7 +140,8 @@ typedef struct ntt_plan ntt_plan;
  * MONT_ERANGE for an unsupported size, MONT_ENOMEM / MONT_ECUDA on failure. */
 int ntt_plan_create(uint32_t p, uint32_t log2n, ntt_plan **out);
 
-/* Frees the plan object (NULL is a no-op).  Its twiddle tables stay cached
+/* Frees the plan object (NULL is a no-op).  Its twiddle tables (the
+ * Montgomery-form roots w^i R mod P of Sec. 3.1's residue map) stay cached
  * in device memory for later plans and products of the same (device, p) and
  * are released with the process; work already queued with the plan may
  * still run. */
@@ -229,7 +230,11 @@ int polymul_noalloc(const ntt_plan *plan, const uint32_t *a, size_t la, const ui
 
 /* ------------------------------------------------------------------------
  * Uneven batches: many products of different lengths and primes in one
- * persistent kernel launch (optionally a CUDA graph replay).
+ * persistent kernel launch, or in the phased form's few kernels (optionally
+ * replayed from a CUDA graph).  The data-parallel REDC of Sec. 3.2 taken from
+ * vector lanes to whole products: every product is the fused NTT product
+ * above (Sec. 1 and 5: the modular FFT libraries), and the autotuner plays the
+ * part of the generator's search over implementations (Sec. 4, 5).
  * ------------------------------------------------------------------------ */
 
 /* One product of a batch: c[0 .. la+lb-1) = a * b mod p.  a, b, c are device
@@ -257,9 +262,10 @@ typedef struct polymul_desc {
  * Kernel forms: the persistent kernel (0, 1) claims jobs from one list and
  * waits, bounded, on per-product counters; the phased form (2) runs each job
  * kind as its own kernel with its own register budget, one CTA per job, in
- * stream order on `stream` plus two side streams the plan owns (small and
- * whole products), joined back before the call's work ends: no device-side
- * waits, and the same results.  Products up to 2^13 run
+ * stream order on `stream` (the forward columns, rows and output columns of
+ * every product above 2^13) plus a side stream the plan owns (the products
+ * up to 2^13, one kernel per size), joined back before the call's work
+ * ends: no device-side waits, and the same results.  Products up to 2^13 run
  * whole in one CTA, products of 2^14 and 2^15 as one whole-product job each,
  * larger ones as column-tile, row and output-tile jobs.  Orders: 0: column
  * tiles first, then whole-product and small jobs, then rows and output
@@ -299,14 +305,22 @@ int polymul_batch_plan_create(const polymul_desc *descs, size_t count, polymul_b
  * descriptor checks; MONT_EINVAL for a bad order or full_transforms. */
 int polymul_batch_describe(const polymul_desc *descs, size_t count, int order, int full_transforms, uint32_t *jobs,
                            size_t cap, uint32_t *prods, size_t *njobs);
+/* Frees the plan and its device tables (NULL is a no-op); queued runs of it
+ * must have finished. */
 void polymul_batch_plan_destroy(polymul_batch_plan *plan);
+/* Bytes of scratch the plan holds (2N words per product with N > 2^13). */
 size_t polymul_batch_plan_workspace_bytes(const polymul_batch_plan *plan);
+/* The plan's current launch configuration; set_config checks the fields
+ * (MONT_EINVAL: ctas_per_sm < 0, order not 0 .. 3, kernel not 0 .. 2,
+ * full_transforms not 0 or 1) and takes effect on the next run. */
 int polymul_batch_plan_get_config(const polymul_batch_plan *plan, polymul_batch_config *cfg);
 int polymul_batch_plan_set_config(polymul_batch_plan *plan, const polymul_batch_config *cfg);
 
 /* Queue the whole batch on `stream`: one memset of the counters and one
- * persistent kernel launch.  The operands must be ready when it runs.  Runs
- * of one plan share its counters and scratch: two of them must not be in
+ * persistent kernel launch (kernel 0, 1), or the phased form's kernels on
+ * `stream` and the plan's side stream, joined back into `stream`
+ * (kernel 2).  The operands must be ready when it runs.  Runs of one plan
+ * share its counters, scratch and side stream: two of them must not be in
  * flight at once (queue them on one stream, or order them with events);
  * distinct plans are independent. */
 int polymul_batch_run(polymul_batch_plan *plan, cudaStream_t stream);
@@ -320,10 +334,13 @@ int polymul_batch_run_graph(polymul_batch_plan *plan, cudaStream_t stream);
  * then incomplete; the device context stays usable). */
 int polymul_batch_status(polymul_batch_plan *plan, cudaStream_t stream);
 
-/* Autotuner: runs the batch `trials` times per launch shape (kernel variant
- * x CTAs per SM x job order), keeps the fastest (CUDA-event timed on `stream`) and caches it
- * for batches with the same size histogram on this device; synchronous.
- * Returns the status of the last run. */
+/* Autotuner (the generator's timing search of Sec. 4, 5, over launch shapes
+ * instead of code variants): runs the batch `trials` times per launch shape
+ * (persistent kernel variant x CTAs per SM x job order, and the phased
+ * form), keeps the fastest (CUDA-event timed on `stream`) and caches it for
+ * batches with the same size histogram on this device; the plan's
+ * full_transforms choice is kept.  Synchronous.  Returns the status of the
+ * last run. */
 int polymul_batch_plan_tune(polymul_batch_plan *plan, cudaStream_t stream, int trials);
 
 /* One-shot batch without a plan: the same persistent kernel and results as
@@ -460,7 +477,8 @@ enum {
 int mont_int_probe(int kind, uint32_t p, uint32_t iterations, uint32_t ctas_per_sm, uint32_t *sink,
                    uint64_t *ops_per_launch, cudaStream_t stream);
 
-/* Static description of a return code; never NULL. */
+/* Static description of a return code (the MONT_E* codes above; the paper
+ * defines no error model); never NULL. */
 const char *mont_strerror(int code);
 
 #ifdef __cplusplus

@@ -89,12 +89,12 @@ int batch_occupancy(int variant, int *per_sm);
 int batch_launch(BatchArgs A, const Job *jobs, uint32_t njobs, size_t sync_words, int grid, int variant,
                  cudaStream_t s);
 // The phased form: the batch's jobs split by kind, each kind its own kernel
-// (one CTA per job), ordered by stream dependencies: small and whole
-// products on two side streams forked from s and joined back, the split
-// products' forward columns, rows and output tiles on s.
+// (one CTA per job), ordered by stream dependencies: the small products on a
+// side stream forked from s and joined back, every larger product's forward
+// columns, rows and output tiles on s.
 struct PhasedHost;
 int batch_launch_phased(BatchArgs A, const PhasedHost &ph, const Job *d_jobs, size_t sync_words, cudaStream_t s,
-                        cudaStream_t aux0, cudaStream_t aux1, cudaEvent_t fork, cudaEvent_t join0, cudaEvent_t join1);
+                        cudaStream_t aux, cudaEvent_t fork, cudaEvent_t join);
 // Scratch words for one product of this output length (0 when N <= 2^13).
 size_t batch_ws_words(size_t lc);
 

@@ -395,4 +395,59 @@ __device__ __forceinline__ void fused_middle_pass(const L (&lay)[2], int tid, co
     }
 }
 
+// ---------------------------------------------------------------- inverse TFT
+
+// x / 2 mod P for x in [0, P): x >> 1, plus (P + 1) / 2 when x is odd.
+__device__ __forceinline__ uint32_t half_mod(uint32_t x, uint32_t p)
+{
+    return (x >> 1) + ((x & 1u) ? (p >> 1) + 1u : 0u);
+}
+
+// Inverse truncated Fourier transform of one column (van der Hoeven's
+// recursion) over node `block I of level S` of the column transform, SIZE
+// entries at x[OFF ..): on entry x[OFF .. OFF + L) holds the node's outputs
+// (bit-reversed order) and x[OFF + L .. OFF + SIZE) its level-S inputs; on
+// return x[OFF .. OFF + SIZE) holds all of its level-S inputs.  The node's
+// butterfly is (x, y) -> (x + r y, x - r y) with r = tw[2^S + I]:
+//  - L >= SIZE/2: the left child's inputs u follow from its (all known)
+//    outputs; the right child's inputs v_j = u_j - 2 r x_{j+h} are known for
+//    j >= L - h, the rest follow from its L - h outputs; then
+//    x_j = (u_j + v_j) / 2 and x_{j+h} = (u_j - v_j) / (2 r);
+//  - L < SIZE/2: for j >= L the left child's input u_j = x_j + r x_{j+h} is
+//    known, the others follow from its L outputs, then x_j = u_j - r x_{j+h}.
+// All values in [0, P); every division is exact (no deferred scale factor).
+// Used by the inverse column passes of truncated products (row-granular
+// TFT): the column transforms are block 0 of levels 0 .. K1-1, so node
+// (S, I) of a column is block I of level S of the whole transform.
+template <int N1, int OFF, int SIZE, int L, int S, int I>
+__device__ __forceinline__ void itft_node(uint32_t (&x)[N1], const uint32_t *__restrict__ tw,
+                                          const uint32_t *__restrict__ itw, Mod m)
+{
+    if constexpr (SIZE > 1 && L > 0) {
+        constexpr int H = SIZE / 2;
+        const uint32_t r = __ldg(tw + (1 << S) + I);   // Montgomery form: REDC(y, r) = y w
+        if constexpr (L >= H) {
+            itft_node<N1, OFF, H, H, S + 1, 2 * I>(x, tw, itw, m);
+            const uint32_t r2 = add_mod(r, r, m.p);
+#pragma unroll
+            for (int j = L - H; j < H; j++)
+                x[OFF + H + j] = sub_mod(x[OFF + j], mont_mul(x[OFF + H + j], r2, m.p, m.pp), m.p);
+            itft_node<N1, OFF + H, H, L - H, S + 1, 2 * I + 1>(x, tw, itw, m);
+            const uint32_t ri = __ldg(itw + (1 << S) + I);
+#pragma unroll
+            for (int j = 0; j < H; j++) {
+                const uint32_t u = x[OFF + j], v = x[OFF + H + j];
+                x[OFF + j] = half_mod(add_mod(u, v, m.p), m.p);
+                x[OFF + H + j] = half_mod(mont_mul(u - v + m.p, ri, m.p, m.pp), m.p);
+            }
+        } else {
+#pragma unroll
+            for (int j = L; j < H; j++) x[OFF + j] = add_mod(x[OFF + j], mont_mul(x[OFF + H + j], r, m.p, m.pp), m.p);
+            itft_node<N1, OFF, H, L, S + 1, 2 * I>(x, tw, itw, m);
+#pragma unroll
+            for (int j = 0; j < H; j++) x[OFF + j] = sub_mod(x[OFF + j], mont_mul(x[OFF + H + j], r, m.p, m.pp), m.p);
+        }
+    }
+}
+
 }  // namespace mont

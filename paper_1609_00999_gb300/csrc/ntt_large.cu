@@ -1,7 +1,7 @@
 // ntt_large.cu -- transforms and products with N = 2^K > 2^14 (up to 2^24).
 //
 // The K levels split into K1 column levels and K2 row levels (K2 = 12 up
-// to K = 16, K - 4 for K = 17, 18, then max(12, K - 10)).  Viewing the N elements as a
+// to K = 16, K - 4 for K = 17, 18, then max(13, K - 10)).  Viewing the N elements as a
 // [2^K1][2^K2] row-major matrix, levels 0 .. K1-1 pair elements of the same
 // column (stride 2^K2) and their twiddles depend only on the row index, so
 // every column is an independent 2^K1-point transform with the table
@@ -51,9 +51,11 @@ struct ColArgs {
     size_t dst_stride;
     int k2;
     const uint32_t *tw;
+    const uint32_t *itw;    // inverse twiddles (the inverse TFT of truncated products)
     uint32_t p, pp;
     uint32_t scale[2];      // nonzero: REDC-multiply inputs by it on load
     uint32_t post;          // nonzero: REDC-multiply outputs by it on store
+    uint32_t rows;          // register column passes store rows t < rows only (truncated products)
 };
 
 template <int K1, bool INVERSE>
@@ -147,7 +149,38 @@ __global__ void __launch_bounds__(kRegColThreads) k_col_regs(ColArgs A, size_t p
             const size_t j = c0 + g * kRegColThreads + (static_cast<size_t>(t) << A.k2);
             uint32_t v = x[g][t];
             if (A.post) v = mont_mul(v, A.post, p, pp);
-            if (j < A.dst_len) dst[j] = v;
+            if (j < A.dst_len && static_cast<uint32_t>(t) < A.rows) dst[j] = v;
+        }
+}
+
+// Inverse column pass of a truncated product (row-granular TFT): the
+// product computed only rows t < L of the 2^K1 rows of 2^k2, so each column
+// holds L known outputs of its column transform and has zero inputs from L
+// on (c is zero from L 2^k2 on); an inverse TFT per column (itft_node)
+// recovers its L inputs, exactly scaled, and writes those below dst_len.
+template <int K1, int L>
+__global__ void __launch_bounds__(kRegColThreads) k_col_regs_itft(ColArgs A, size_t prod0)
+{
+    constexpr int N1 = 1 << K1, G = 16 / N1;
+    const size_t prod = prod0 + blockIdx.z;
+    const uint32_t *src = A.src[0] + prod * A.src_stride[0];
+    uint32_t *dst = A.dst[0] + prod * A.dst_stride;
+    const Mod md{A.p, A.pp};
+    const size_t c0 = static_cast<size_t>(blockIdx.x) * (kRegColThreads * G) + threadIdx.x;
+    uint32_t x[G][N1];
+#pragma unroll
+    for (int g = 0; g < G; g++)
+#pragma unroll
+        for (int t = 0; t < N1; t++)
+            x[g][t] = t < L ? __ldg(src + c0 + g * kRegColThreads + (static_cast<size_t>(t) << A.k2)) : 0u;
+#pragma unroll
+    for (int g = 0; g < G; g++) itft_node<N1, 0, N1, L, 0, 0>(x[g], A.tw, A.itw, md);
+#pragma unroll
+    for (int g = 0; g < G; g++)
+#pragma unroll
+        for (int t = 0; t < L; t++) {
+            const size_t j = c0 + g * kRegColThreads + (static_cast<size_t>(t) << A.k2);
+            if (j < A.dst_len) dst[j] = x[g][t];
         }
 }
 
@@ -268,11 +301,10 @@ int launch_col_regs(const ColArgs &A, size_t nops, size_t count, cudaStream_t s)
 }
 
 template <int K2>
-int launch_row_polymul(const RowArgs &A, size_t count, cudaStream_t s)
+int launch_row_polymul(const RowArgs &A, size_t count, cudaStream_t s, uint32_t rows)
 {
     const size_t smem = team_smem_words<K2>() * sizeof(uint32_t);
     if (ensure_smem(k_row_polymul<K2>, smem) != MONT_OK) return MONT_ECUDA;
-    const unsigned rows = static_cast<unsigned>(A.n >> K2);
     for (size_t first = 0; first < count; first += kMaxGridZ) {
         const unsigned y = static_cast<unsigned>(std::min<size_t>(kMaxGridZ, count - first));
         k_row_polymul<K2><<<dim3(rows, y), nt_of<K2>(), smem, s>>>(A, first);
@@ -297,13 +329,14 @@ int launch_row_ntt(const RowNttArgs &A, size_t count, cudaStream_t s)
 
 // Row levels K2: 2^12 rows up to N = 2^16; rows of 2^13 and 2^14 for
 // N = 2^17 and 2^18, which keeps four column levels (register column
-// passes); beyond, 2^12 rows again (rows of 2^14, one CTA per SM, measured
-// no faster there) until K - 10 > 12.
+// passes); beyond, rows of 2^13 (measured against rows of 2^12 and 2^14 for
+// N = 2^19, 2^20, 2^21: 1-6 % faster, the shared-memory column tiles then
+// one level shorter) until K - 10 > 13.
 int split_k2(int k)
 {
     if (k <= 16) return 12;
     if (k <= 18) return k - 4;
-    return std::max(12, k - 10);
+    return std::max(13, k - 10);
 }
 
 #define MONT_K1_TILE_CASES(X) X(5) X(6) X(7) X(8) X(9) X(10)
@@ -324,12 +357,12 @@ int dispatch_col(int k1, const ColArgs &A, size_t nops, size_t count, cudaStream
     }
 }
 
-int dispatch_row_polymul(int k2, const RowArgs &A, size_t count, cudaStream_t s)
+int dispatch_row_polymul(int k2, const RowArgs &A, size_t count, cudaStream_t s, uint32_t rows)
 {
     switch (k2) {
-    case 12: return launch_row_polymul<12>(A, count, s);
-    case 13: return launch_row_polymul<13>(A, count, s);
-    case 14: return launch_row_polymul<14>(A, count, s);
+    case 12: return launch_row_polymul<12>(A, count, s, rows);
+    case 13: return launch_row_polymul<13>(A, count, s, rows);
+    case 14: return launch_row_polymul<14>(A, count, s, rows);
     default: return MONT_EUNSUPPORTED;
     }
 }
@@ -341,6 +374,39 @@ int dispatch_row_ntt(int k2, const RowNttArgs &A, size_t count, cudaStream_t s)
     case 12: return launch_row_ntt<12, INVERSE>(A, count, s);
     case 13: return launch_row_ntt<13, INVERSE>(A, count, s);
     case 14: return launch_row_ntt<14, INVERSE>(A, count, s);
+    default: return MONT_EUNSUPPORTED;
+    }
+}
+
+template <int K1, int L>
+int launch_col_itft(const ColArgs &A, size_t count, cudaStream_t s)
+{
+    constexpr int COLS = kRegColThreads * (16 >> K1);
+    const size_t n2 = size_t{1} << A.k2;
+    for (size_t first = 0; first < count; first += kMaxGridZ) {
+        const unsigned z = static_cast<unsigned>(std::min<size_t>(kMaxGridZ, count - first));
+        k_col_regs_itft<K1, L><<<dim3(static_cast<unsigned>(n2 / COLS), 1, z), kRegColThreads, 0, s>>>(A, first);
+        if (cudaGetLastError() != cudaSuccess) return MONT_ECUDA;
+    }
+    return MONT_OK;
+}
+
+// Inverse TFT column pass for K1 column levels of which `rows` rows were
+// computed, 2^(K1-1) < rows < 2^K1.
+int dispatch_col_itft(int k1, uint32_t rows, const ColArgs &A, size_t count, cudaStream_t s)
+{
+    switch (k1 * 16 + static_cast<int>(rows)) {
+    case 2 * 16 + 3: return launch_col_itft<2, 3>(A, count, s);
+    case 3 * 16 + 5: return launch_col_itft<3, 5>(A, count, s);
+    case 3 * 16 + 6: return launch_col_itft<3, 6>(A, count, s);
+    case 3 * 16 + 7: return launch_col_itft<3, 7>(A, count, s);
+    case 4 * 16 + 9: return launch_col_itft<4, 9>(A, count, s);
+    case 4 * 16 + 10: return launch_col_itft<4, 10>(A, count, s);
+    case 4 * 16 + 11: return launch_col_itft<4, 11>(A, count, s);
+    case 4 * 16 + 12: return launch_col_itft<4, 12>(A, count, s);
+    case 4 * 16 + 13: return launch_col_itft<4, 13>(A, count, s);
+    case 4 * 16 + 14: return launch_col_itft<4, 14>(A, count, s);
+    case 4 * 16 + 15: return launch_col_itft<4, 15>(A, count, s);
     default: return MONT_EUNSUPPORTED;
     }
 }
@@ -364,6 +430,19 @@ int polymul_large(const ntt_plan &plan, const uint32_t *a, size_t la, const uint
 {
     const int k = plan.log2n, k2 = split_k2(k), k1 = k - k2;
     const size_t n = size_t{1} << k;
+    // Row-granular truncated transform (as in the batches): with register
+    // column passes (2 <= K1 <= 4), compute only the ceil(lc / 2^K2) rows the
+    // output reaches, and invert each column with an inverse TFT; b is then
+    // scaled by (2^K2)^-1 R^2, since the inverse column pass scales exactly.
+    const size_t lc = la + lb - 1;
+    const uint32_t rows_all = 1u << k1;
+    const uint32_t need = static_cast<uint32_t>((lc + (size_t{1} << k2) - 1) >> k2);
+    const bool tft = k1 >= 2 && k1 <= 4 && need < rows_all;
+    uint32_t k_scale = plan.k_scale;
+    if (tft) {
+        const uint32_t m_mod = static_cast<uint32_t>((uint64_t{1} << k2) % plan.p);
+        k_scale = host_to_mont(host_to_mont(host_powmod(m_mod, plan.p - 2, plan.p), plan.p), plan.p);
+    }
     ColArgs F{};
     F.src[0] = a;
     F.src[1] = b;
@@ -380,12 +459,13 @@ int polymul_large(const ntt_plan &plan, const uint32_t *a, size_t la, const uint
     F.p = plan.p;
     F.pp = plan.p_prime;
     F.scale[0] = 0;
-    F.scale[1] = plan.k_scale;
+    F.scale[1] = k_scale;
     F.post = 0;
+    F.rows = tft ? need : rows_all;
     int rc = dispatch_col<false>(k1, F, 2, count, s);
     if (rc != MONT_OK) return rc;
     RowArgs R{ws, n, k1, plan.table->fwd, plan.table->inv, plan.p, plan.p_prime};
-    rc = dispatch_row_polymul(k2, R, count, s);
+    rc = dispatch_row_polymul(k2, R, count, s, tft ? need : rows_all);
     if (rc != MONT_OK) return rc;
     ColArgs I{};
     I.src[0] = I.src[1] = ws;
@@ -398,6 +478,12 @@ int polymul_large(const ntt_plan &plan, const uint32_t *a, size_t la, const uint
     I.tw = plan.table->inv;
     I.p = plan.p;
     I.pp = plan.p_prime;
+    I.rows = rows_all;
+    if (tft) {
+        I.tw = plan.table->fwd;   // itft_node takes both tables
+        I.itw = plan.table->inv;
+        return dispatch_col_itft(k1, need, I, count, s);
+    }
     return dispatch_col<true>(k1, I, 1, count, s);
 }
 
@@ -416,6 +502,7 @@ int ntt_large(const ntt_plan *plan, uint32_t *data, size_t batch, int flags, boo
     C.k2 = k2;
     C.p = plan->p;
     C.pp = plan->p_prime;
+    C.rows = 1u << k1;
     RowNttArgs R{data, n, k1, nullptr, plan->p, plan->p_prime};
     int rc;
     if (!inverse) {

@@ -280,56 +280,6 @@ __device__ __forceinline__ void col_regs(const Prod &P, const PrimeInfo &pr, uin
     }
 }
 
-// x / 2 mod P for x in [0, P): x >> 1, plus (P + 1) / 2 when x is odd.
-__device__ __forceinline__ uint32_t half_mod(uint32_t x, uint32_t p)
-{
-    return (x >> 1) + ((x & 1u) ? (p >> 1) + 1u : 0u);
-}
-
-// Inverse truncated Fourier transform of one column (van der Hoeven's
-// recursion) over node `block I of level S` of the column transform, SIZE
-// entries at x[OFF ..): on entry x[OFF .. OFF + L) holds the node's outputs
-// (bit-reversed order) and x[OFF + L .. OFF + SIZE) its level-S inputs; on
-// return x[OFF .. OFF + SIZE) holds all of its level-S inputs.  The node's
-// butterfly is (x, y) -> (x + r y, x - r y) with r = tw[2^S + I]:
-//  - L >= SIZE/2: the left child's inputs u follow from its (all known)
-//    outputs; the right child's inputs v_j = u_j - 2 r x_{j+h} are known for
-//    j >= L - h, the rest follow from its L - h outputs; then
-//    x_j = (u_j + v_j) / 2 and x_{j+h} = (u_j - v_j) / (2 r);
-//  - L < SIZE/2: for j >= L the left child's input u_j = x_j + r x_{j+h} is
-//    known, the others follow from its L outputs, then x_j = u_j - r x_{j+h}.
-// All values in [0, P); every division is exact (no deferred scale factor).
-template <int N1, int OFF, int SIZE, int L, int S, int I>
-__device__ __forceinline__ void itft_node(uint32_t (&x)[N1], const uint32_t *__restrict__ tw,
-                                          const uint32_t *__restrict__ itw, Mod m)
-{
-    if constexpr (SIZE > 1 && L > 0) {
-        constexpr int H = SIZE / 2;
-        const uint32_t r = __ldg(tw + (1 << S) + I);   // Montgomery form: REDC(y, r) = y w
-        if constexpr (L >= H) {
-            itft_node<N1, OFF, H, H, S + 1, 2 * I>(x, tw, itw, m);
-            const uint32_t r2 = add_mod(r, r, m.p);
-#pragma unroll
-            for (int j = L - H; j < H; j++)
-                x[OFF + H + j] = sub_mod(x[OFF + j], mont_mul(x[OFF + H + j], r2, m.p, m.pp), m.p);
-            itft_node<N1, OFF + H, H, L - H, S + 1, 2 * I + 1>(x, tw, itw, m);
-            const uint32_t ri = __ldg(itw + (1 << S) + I);
-#pragma unroll
-            for (int j = 0; j < H; j++) {
-                const uint32_t u = x[OFF + j], v = x[OFF + H + j];
-                x[OFF + j] = half_mod(add_mod(u, v, m.p), m.p);
-                x[OFF + H + j] = half_mod(mont_mul(u - v + m.p, ri, m.p, m.pp), m.p);
-            }
-        } else {
-#pragma unroll
-            for (int j = L; j < H; j++) x[OFF + j] = add_mod(x[OFF + j], mont_mul(x[OFF + H + j], r, m.p, m.pp), m.p);
-            itft_node<N1, OFF, H, L, S + 1, 2 * I>(x, tw, itw, m);
-#pragma unroll
-            for (int j = 0; j < H; j++) x[OFF + j] = sub_mod(x[OFF + j], mont_mul(x[OFF + H + j], r, m.p, m.pp), m.p);
-        }
-    }
-}
-
 // Inverse column pass of a truncated split product (K1 <= 4 column levels,
 // L = nrows rows computed): the columns of reg_cols(K1) consecutive columns,
 // each an inverse TFT of its L known outputs (the rows) with its inputs
@@ -603,13 +553,15 @@ __global__ void __launch_bounds__(kThreads, MINB) k_polymul_batch(BatchArgs A)
 
 // ---------------------------------------------------------------- phased form
 //
-// The same jobs as separate kernels, one CTA per job (or per team of small
-// products), ordered by stream dependencies instead of device-side waits:
-// every kernel gets the register budget of its own job kind.  A batch runs
-// as: small products (one kernel per size, N <= 2^13) and whole products
-// (2^14, 2^15) on side branches, and the split products' forward column
-// tiles, then their rows, then their output tiles on the main branch; the
-// host joins the branches (polymul_batch_run / the graph of
+// The same products as separate kernels, one CTA per job (or per team of
+// small products), ordered by stream dependencies instead of device-side
+// waits: every kernel gets the register budget of its own job kind.  A
+// batch runs as: small products (one kernel per size, N <= 2^13) on a side
+// branch, and every larger product's forward column tiles, then its rows,
+// then its output tiles on the main branch (products of 2^14 and 2^15 too:
+// without waits to avoid, splitting them is 1 % faster for the uneven
+// workload than one CTA per product recomputing its column levels row by
+// row); the host joins the branches (polymul_batch_run / the graph of
 // polymul_batch_run_graph).  No kernel waits on another's progress.
 
 // Products prods[first .. first + count), all of size 2^K (K <= 13), one
@@ -628,14 +580,6 @@ k_phase_small(BatchArgs A, uint32_t first, uint32_t count)
     polymul_team<K, true, true, NT>(smem + team * team_smem_words<K>(), tid, P.a, valid ? P.la : 0, P.b,
                                     valid ? P.lb : 0, P.c, valid ? P.lc : 0, pr.tw, pr.itw, 0, 0, pr.p, pr.pp,
                                     P.k_scale);
-}
-
-// Whole-product jobs (2^14, 2^15), one CTA each: A.jobs lists them.
-__global__ void __launch_bounds__(kThreads, 3) k_phase_whole(BatchArgs A)
-{
-    extern __shared__ __align__(16) uint32_t smem[];
-    const Prod &P = A.prods[A.jobs[blockIdx.x].prod];
-    whole_dispatch(smem, P, A.primes[P.prime]);
 }
 
 // Row jobs of split products, one CTA each (their column tiles are done).
@@ -871,7 +815,7 @@ int batch_occupancy(int variant, int *per_sm)
 }
 
 // Jobs of one batch split by the phased form's kernels.
-enum PhaseList { PH_WHOLE = 0, PH_COLF_REG, PH_COLF_TILE, PH_ROW, PH_COLI_REG, PH_COLI_TILE, PH_LISTS };
+enum PhaseList { PH_COLF_REG = 0, PH_COLF_TILE, PH_ROW, PH_COLI_REG, PH_COLI_TILE, PH_LISTS };
 
 struct PhasedHost {
     std::vector<Job> jobs;            // the lists back to back
@@ -885,7 +829,13 @@ void phased_build(const BatchHost &b, PhasedHost &out)
     for (const Job &J : b.jobs[0]) {
         const bool reg = J.k - kRowLog <= static_cast<uint32_t>(kMaxRegColLog);
         switch (J.type) {
-        case JOB_WHOLE: lists[PH_WHOLE].push_back(J); break;
+        case JOB_WHOLE: {   // column / row / column jobs here (K1 = 1, 2: register columns)
+            const Prod &P = b.prods[J.prod];
+            for (uint32_t t = 0; t < P.ntiles; t++) lists[PH_COLF_REG].push_back(Job{JOB_COLF, P.k, J.prod, t});
+            for (uint32_t r = 0; r < P.nrows; r++) lists[PH_ROW].push_back(Job{JOB_ROW, P.k, J.prod, r});
+            for (uint32_t t = 0; t < P.ntiles; t++) lists[PH_COLI_REG].push_back(Job{JOB_COLI, P.k, J.prod, t});
+            break;
+        }
         case JOB_COLF: lists[reg ? PH_COLF_REG : PH_COLF_TILE].push_back(J); break;
         case JOB_ROW: lists[PH_ROW].push_back(J); break;
         case JOB_COLI: lists[reg ? PH_COLI_REG : PH_COLI_TILE].push_back(J); break;
@@ -944,27 +894,24 @@ int phase_jobs(K kernel, BatchArgs A, const Job *jobs, uint32_t count, size_t sm
 }  // namespace
 
 int batch_launch_phased(BatchArgs A, const PhasedHost &ph, const Job *d_jobs, size_t sync_words, cudaStream_t s,
-                        cudaStream_t aux0, cudaStream_t aux1, cudaEvent_t fork, cudaEvent_t join0, cudaEvent_t join1)
+                        cudaStream_t aux, cudaEvent_t fork, cudaEvent_t join)
 {
     if (cudaMemsetAsync(A.sync, 0, sync_words * sizeof(uint32_t), s) != cudaSuccess) return MONT_ECUDA;
-    if (cudaEventRecord(fork, s) != cudaSuccess || cudaStreamWaitEvent(aux0, fork, 0) != cudaSuccess ||
-        cudaStreamWaitEvent(aux1, fork, 0) != cudaSuccess)
+    if (cudaEventRecord(fork, s) != cudaSuccess || cudaStreamWaitEvent(aux, fork, 0) != cudaSuccess)
         return MONT_ECUDA;
     int rc = MONT_OK;
     for (size_t i = 0; i + 2 < ph.small.size() && rc == MONT_OK; i += 3)
-        rc = phase_small(static_cast<int>(ph.small[i]), A, ph.small[i + 1], ph.small[i + 2], aux0);
+        rc = phase_small(static_cast<int>(ph.small[i]), A, ph.small[i + 1], ph.small[i + 2], aux);
     const size_t smem = kSmemWords * sizeof(uint32_t);
     auto list = [&](int l) { return d_jobs + ph.off[l]; };
-    if (rc == MONT_OK) rc = phase_jobs(k_phase_whole, A, list(PH_WHOLE), ph.cnt[PH_WHOLE], smem, aux1);
     if (rc == MONT_OK) rc = phase_jobs(k_phase_col_regs<false>, A, list(PH_COLF_REG), ph.cnt[PH_COLF_REG], 0, s);
     if (rc == MONT_OK) rc = phase_jobs(k_phase_col_tile<false>, A, list(PH_COLF_TILE), ph.cnt[PH_COLF_TILE], smem, s);
     if (rc == MONT_OK) rc = phase_jobs(k_phase_row, A, list(PH_ROW), ph.cnt[PH_ROW], smem, s);
     if (rc == MONT_OK) rc = phase_jobs(k_phase_col_regs<true>, A, list(PH_COLI_REG), ph.cnt[PH_COLI_REG], 0, s);
     if (rc == MONT_OK) rc = phase_jobs(k_phase_col_tile<true>, A, list(PH_COLI_TILE), ph.cnt[PH_COLI_TILE], smem, s);
-    // Join the side branches back into s (also after a failed launch, so no
+    // Join the side branch back into s (also after a failed launch, so no
     // branch is left open in a capture).
-    const bool joined = cudaEventRecord(join0, aux0) == cudaSuccess && cudaEventRecord(join1, aux1) == cudaSuccess &&
-                        cudaStreamWaitEvent(s, join0, 0) == cudaSuccess && cudaStreamWaitEvent(s, join1, 0) == cudaSuccess;
+    const bool joined = cudaEventRecord(join, aux) == cudaSuccess && cudaStreamWaitEvent(s, join, 0) == cudaSuccess;
     return rc != MONT_OK ? rc : (joined ? MONT_OK : MONT_ECUDA);
 }
 
@@ -997,8 +944,8 @@ struct polymul_batch_plan {
     mont::Prod *d_prods[2] = {};
     mont::PhasedHost phased[2];              // the phased form's job lists (kernel 2)
     mont::Job *d_phased[2] = {};
-    cudaStream_t aux[2] = {};
-    cudaEvent_t ev_fork = nullptr, ev_join[2] = {};
+    cudaStream_t aux = nullptr;              // the phased form's side stream (small products)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     uint32_t *d_sync = nullptr;
     size_t sync_words = 0;
     uint32_t *d_ws = nullptr;
@@ -1034,11 +981,9 @@ void free_plan(polymul_batch_plan *pl)
         for (mont::Job *j : v) cudaFree(j);
     for (mont::Prod *d : pl->d_prods) cudaFree(d);
     for (mont::Job *j : pl->d_phased) cudaFree(j);
-    for (cudaStream_t a : pl->aux)
-        if (a) cudaStreamDestroy(a);
+    if (pl->aux) cudaStreamDestroy(pl->aux);
     if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
-    for (cudaEvent_t e : pl->ev_join)
-        if (e) cudaEventDestroy(e);
+    if (pl->ev_join) cudaEventDestroy(pl->ev_join);
     cudaFree(pl->d_sync);
     cudaFree(pl->d_ws);
 }
@@ -1051,8 +996,8 @@ int launch(polymul_batch_plan *pl, const polymul_batch_config &cfg, cudaStream_t
     if (cfg.kernel == 2) {
         BatchArgs A = pl->args;
         A.prods = pl->d_prods[full];
-        return batch_launch_phased(A, pl->phased[full], pl->d_phased[full], pl->sync_words, s, pl->aux[0], pl->aux[1],
-                                   pl->ev_fork, pl->ev_join[0], pl->ev_join[1]);
+        return batch_launch_phased(A, pl->phased[full], pl->d_phased[full], pl->sync_words, s, pl->aux, pl->ev_fork,
+                                   pl->ev_join);
     }
     const int occ = pl->occ[variant];
     const int per_sm = std::max(1, std::min(cfg.ctas_per_sm > 0 ? cfg.ctas_per_sm : occ, occ));
@@ -1141,10 +1086,10 @@ extern "C" int polymul_batch_plan_create(const polymul_desc *descs, size_t count
                                 cudaMemcpyHostToDevice) == cudaSuccess;
     }
     if (ok) ok = batch_occupancy(0, &pl->occ[0]) == MONT_OK && batch_occupancy(1, &pl->occ[1]) == MONT_OK;
-    for (int i = 0; i < 2 && ok; i++)
-        ok = cudaStreamCreateWithFlags(&pl->aux[i], cudaStreamNonBlocking) == cudaSuccess &&
-             cudaEventCreateWithFlags(&pl->ev_join[i], cudaEventDisableTiming) == cudaSuccess;
-    if (ok) ok = cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    if (ok)
+        ok = cudaStreamCreateWithFlags(&pl->aux, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&pl->ev_join, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming) == cudaSuccess;
     pl->occupancy = pl->occ[0];
     pl->sms = device_sm_count();
     if (!ok || pl->sms <= 0) {

@@ -102,3 +102,29 @@ def test_large_polymul_many_and_chunked_workspace(m):
     with pytest.raises(m.MontError) as e:
         m.polymul_many_ws(p, to_dev(a), to_dev(b), small)
     assert e.value.code == m.MONT_EINVAL
+
+
+# Single-call products of N = 2^15 .. 2^18 on both sides of the row counts
+# of the truncated transforms (rows of 2^12 up to N = 2^16, 2^13 for 2^17,
+# 2^14 for 2^18; a product computes ceil(lc / row) rows when that is fewer
+# than all of them): the first and last row counts that save a row, exact
+# multiples of the row, one past, and asymmetric operands.
+TFT_SINGLE = [(16385, 1), (20000, 5000), (14336, 14337), (14337, 14337), (30000, 2769), (1, 32769),
+              (40000, 1), (32768, 28673), (65536, 1), (70000, 1), (61440, 61441), (100000, 31073),
+              (140000, 1), (180000, 20001), (200000, 50000)]
+
+
+@pytest.mark.parametrize("la,lb", TFT_SINGLE)
+def test_truncated_single_products(m, la, lb):
+    p = synth.PRIMES[(la + lb) % 3]
+    a = synth.residues(la, p, 320, la, lb, 0)
+    b = synth.residues(lb, p, 320, la, lb, 1)
+    ref = oracle.polymul_ntt(p, a, b)
+    assert np.array_equal(to_host(m.polymul(p, to_dev(a), to_dev(b))), ref)
+    if la + lb <= 120000:                       # three at once, each against the oracle
+        import torch
+        a3 = np.stack([a, np.roll(a, 1), np.roll(a, 2)])
+        b3 = np.stack([b, np.roll(b, 3), np.roll(b, 5)])
+        got = to_host(m.polymul_many(p, to_dev(a3), to_dev(b3))).reshape(3, la + lb - 1)
+        for i in range(3):
+            assert np.array_equal(got[i], oracle.polymul_ntt(p, a3[i], b3[i])), i
