@@ -391,7 +391,7 @@ def ntt_transforms(m, torch, peaks, steps=10, warmup=3):
             counts = add_counts({}, op_counts_ntt(n, k == "inv"), rows)
             kern = ("k_ntt_%s<%d>" % (k, logn)) if logn <= 14 else "ntt_%s 2^%d (column, row kernels)" % (k, logn)
             r[k] = {"ms": ms, "value": rows * n / ms / 1e6,
-                    "roofline": int_roofline(kern, ops, counts, ms, peaks),
+                    "roofline": int_roofline(kern, ops, counts, ms, peaks, traffic_units=rows),
                     "hbm_gbs_at_pass_count": rows * n * 8 * passes / (ms / 1e3) / 1e9}
         res["N%d_x%d" % (n, rows)] = r
         del d
