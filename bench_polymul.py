@@ -556,6 +556,10 @@ def uneven_batch(m, torch, peaks, steps=10, warmup=3, cpu=True, per_product=True
                                       "peak_gbs": peaks["hbm_gbs"],
                                       "frac": hbm / (t_ms / 1e3) / 1e9 / peaks["hbm_gbs"]}}
 
+    # Kernels one run launches: the persistent kernel, or the phased form's
+    # kernel per small-product size plus its three column / row kernels.
+    small_sizes = {n for n in ns if n <= 1 << 13}
+    kernels_per_run = len(small_sizes) + 3 if cfg.kernel == 2 else 1
     tft = figures(ms, True)
     full = figures(ms_full, False)
     n_trunc = sum(1 for n, lc in zip(ns, lcs) if tft_rows(n, int(lc)) is not None)
@@ -568,7 +572,7 @@ def uneven_batch(m, torch, peaks, steps=10, warmup=3, cpu=True, per_product=True
            "tuned_config": {"ctas_per_sm": cfg.ctas_per_sm, "order": cfg.order, "kernel": cfg.kernel,
                             "full_transforms": cfg.full_transforms, "tuned": config is None}, "tune_s": tune_s,
            "workspace_bytes": plan.workspace_bytes(), "l2": "operands + scratch (2.4 GB) larger than L2",
-           "gpu_launches": 2 * (steps + warmup),
+           "gpu_launches": 2 * (steps + warmup) * kernels_per_run, "kernels_per_run": kernels_per_run,
            "roofline": tft["roofline"],
            "hbm_at_pass_count": dict(tft["hbm_at_pass_count"],
                                      passes="one for N <= 2^13; operands, results and the product rows' scratch "
