@@ -92,7 +92,16 @@ int batch_launch(BatchArgs A, const Job *jobs, uint32_t njobs, size_t sync_words
 // (one CTA per job), ordered by stream dependencies: the small products on a
 // side stream forked from s and joined back, every larger product's forward
 // columns, rows and output tiles on s.
-struct PhasedHost;
+enum PhaseList { PH_COLF_REG = 0, PH_COLF_TILE, PH_ROW, PH_COLI_REG, PH_COLI_TILE, PH_LISTS };
+
+struct PhasedHost {
+    std::vector<Job> jobs;            // the lists back to back
+    uint32_t off[PH_LISTS] = {}, cnt[PH_LISTS] = {};
+    std::vector<uint32_t> small;      // (log2 N, first product, count) per size present
+};
+
+// Splits a built batch's products into the phased form's lists.
+void phased_build(const BatchHost &b, PhasedHost &out);
 int batch_launch_phased(BatchArgs A, const PhasedHost &ph, const Job *d_jobs, size_t sync_words, cudaStream_t s,
                         cudaStream_t aux, cudaEvent_t fork, cudaEvent_t join);
 // Scratch words for one product of this output length (0 when N <= 2^13).

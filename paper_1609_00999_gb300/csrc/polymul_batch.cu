@@ -814,15 +814,6 @@ int batch_occupancy(int variant, int *per_sm)
     return *per_sm > 0 ? MONT_OK : MONT_ECUDA;
 }
 
-// Jobs of one batch split by the phased form's kernels.
-enum PhaseList { PH_COLF_REG = 0, PH_COLF_TILE, PH_ROW, PH_COLI_REG, PH_COLI_TILE, PH_LISTS };
-
-struct PhasedHost {
-    std::vector<Job> jobs;            // the lists back to back
-    uint32_t off[PH_LISTS] = {}, cnt[PH_LISTS] = {};
-    std::vector<uint32_t> small;      // (log2 N, first product, count) per size present
-};
-
 void phased_build(const BatchHost &b, PhasedHost &out)
 {
     std::vector<Job> lists[PH_LISTS];

@@ -37,6 +37,9 @@ namespace {
 
 constexpr size_t kAlign = 256;
 constexpr int kServeOrder = 0;   // job order: column tiles, whole and small products, rows, output tiles
+// Batch form: the phased form (one kernel per job kind, small products on a
+// side stream of the slot) or the persistent kernel.
+constexpr bool kServePhased = true;
 
 // First-fit allocator over one device region, offsets in bytes.
 class Arena {
@@ -146,6 +149,9 @@ struct Slot {
     size_t cap_copy = 0;
     std::vector<CopyDesc> copies;
     BatchHost host;
+    PhasedHost phased;
+    cudaStream_t aux = nullptr;                 // the phased form's side stream
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 size_t words_bytes(size_t w)
@@ -312,7 +318,8 @@ int issue_batch(mont_server *sv, Slot &s)
         for (const Req &q : s.reqs) ws_of[q.dc] = q.dws;
         for (Prod &P : s.host.prods)
             if (P.k > static_cast<uint32_t>(kSmallLog)) P.ws = ws_of[P.c];
-        rc = grow_slot(s, s.host.jobs[kServeOrder].size(), s.host.prods.size());
+        if (kServePhased) phased_build(s.host, s.phased);
+        rc = grow_slot(s, kServePhased ? s.phased.jobs.size() : s.host.jobs[kServeOrder].size(), s.host.prods.size());
     }
     // Small requests' copies as descriptor lists for the copy kernel: operands
     // first [0, ngather), results after.
@@ -338,13 +345,14 @@ int issue_batch(mont_server *sv, Slot &s)
                 rc = MONT_ECUDA;
         }
         std::copy(s.copies.begin(), s.copies.end(), s.h_copy);
-        std::copy(s.host.jobs[kServeOrder].begin(), s.host.jobs[kServeOrder].end(), s.h_jobs);
+        const std::vector<Job> &jobs = kServePhased ? s.phased.jobs : s.host.jobs[kServeOrder];
+        std::copy(jobs.begin(), jobs.end(), s.h_jobs);
         std::copy(s.host.prods.begin(), s.host.prods.end(), s.h_prods);
         if (rc == MONT_OK &&
             ((!s.copies.empty() && cudaMemcpyAsync(s.d_copy, s.h_copy, s.copies.size() * sizeof(CopyDesc),
                                                    cudaMemcpyHostToDevice, s.stream) != cudaSuccess) ||
-             cudaMemcpyAsync(s.d_jobs, s.h_jobs, s.host.jobs[kServeOrder].size() * sizeof(Job), cudaMemcpyHostToDevice,
-                             s.stream) != cudaSuccess ||
+             (!jobs.empty() && cudaMemcpyAsync(s.d_jobs, s.h_jobs, jobs.size() * sizeof(Job), cudaMemcpyHostToDevice,
+                                               s.stream) != cudaSuccess) ||
              cudaMemcpyAsync(s.d_prods, s.h_prods, s.host.prods.size() * sizeof(Prod), cudaMemcpyHostToDevice,
                              s.stream) != cudaSuccess))
             rc = MONT_ECUDA;
@@ -359,8 +367,12 @@ int issue_batch(mont_server *sv, Slot &s)
         BatchArgs A = sv->args;
         A.prods = s.d_prods;
         A.sync = s.d_sync;
-        rc = batch_launch(A, s.d_jobs, static_cast<uint32_t>(s.host.jobs[kServeOrder].size()), 2 + 2 * s.host.prods.size(),
-                          sv->sms * sv->occupancy, 1, s.stream);
+        if (kServePhased)
+            rc = batch_launch_phased(A, s.phased, s.d_jobs, 2 + 2 * s.host.prods.size(), s.stream, s.aux, s.ev_fork,
+                                     s.ev_join);
+        else
+            rc = batch_launch(A, s.d_jobs, static_cast<uint32_t>(s.host.jobs[kServeOrder].size()),
+                              2 + 2 * s.host.prods.size(), sv->sms * sv->occupancy, 1, s.stream);
     }
     if (rc == MONT_OK) {
         const size_t nscatter = s.copies.size() - ngather;
@@ -422,6 +434,9 @@ void destroy_server(mont_server *sv)
         cudaFree(s.d_copy);
         cudaFreeHost(s.h_copy);
         if (s.done) cudaEventDestroy(s.done);
+        if (s.ev_fork) cudaEventDestroy(s.ev_fork);
+        if (s.ev_join) cudaEventDestroy(s.ev_join);
+        if (s.aux) cudaStreamDestroy(s.aux);
         if (s.stream) cudaStreamDestroy(s.stream);
     }
     cudaFree(sv->arena_base);
@@ -459,7 +474,10 @@ extern "C" int mont_server_create(const uint32_t *primes, int nprimes, uint32_t 
     for (int i = 0; i < slots && rc == MONT_OK; i++) {
         Slot &s = *sv->slots[i];
         if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&s.aux, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&s.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&s.ev_join, cudaEventDisableTiming) != cudaSuccess ||
             cudaMallocHost(&s.h_err, sizeof(uint32_t)) != cudaSuccess)
             rc = MONT_ECUDA;
         else
