@@ -231,95 +231,6 @@ k_row_ntt(RowNttArgs A, size_t prod0)
     for (int k = threadIdx.x; k < N2; k += NT) g[k] = INVERSE ? lay[0][k] : csub(lay[0][k], A.p);
 }
 
-// Natural-order transforms without a separate bit-reversal pass.  After the
-// row levels, position j of row r holds X_(brev(j) 2^K1 + brev(r)), so the
-// natural order interleaves rows at the finest grain.  A CTA of kNatTeams
-// teams takes the kNatRows rows whose bit-reversed indices are kNatRows
-// consecutive numbers v0 .. v0 + 7: for each u their outputs fill the 32
-// consecutive bytes u 2^K1 + v0 .. + 7.  The rows sit in shared memory at a
-// stride of the padded row plus 4 words, so that a warp covering 8 rows and
-// 4 values of u, a quarter of the row apart, touches 32 distinct banks
-// (counted on the host).  The kernels cannot work in place (a CTA's
-// transposed stores land in rows other CTAs still read), so the forward
-// reads the column kernel's output from scratch and writes the data, and
-// the inverse reads the data and writes rows to scratch for the column
-// kernel.
-constexpr int kNatRows = 8, kNatTeams = 4;
-
-struct RowNatArgs {
-    const uint32_t *src;
-    uint32_t *dst;
-    size_t n;        // words per transform, in src and dst
-    int k1;
-    const uint32_t *tw;
-    uint32_t p, pp;
-};
-
-template <int K2>
-constexpr int nat_row_words()
-{
-    return PadLayout::words(1 << K2) + 4;
-}
-
-__device__ __forceinline__ int brev_n(int x, int bits)
-{
-    return bits == 0 ? 0 : static_cast<int>(__brev(static_cast<unsigned>(x)) >> (32 - bits));
-}
-
-template <int K2, bool INVERSE>
-__global__ void __launch_bounds__(kNatTeams * nt_of<K2>()) k_row_ntt_nat(RowNatArgs A, size_t prod0)
-{
-    constexpr int N2 = 1 << K2, NT = nt_of<K2>(), NP = SchedFor<K2, NT>::kPasses, RW = nat_row_words<K2>();
-    constexpr int THREADS = kNatTeams * NT, PER = kNatRows * N2 / THREADS;
-    static_assert(kNatRows == 8 && (kNatRows * N2) % THREADS == 0, "transposed tile");
-    extern __shared__ __align__(16) uint32_t smem[];
-    const int team = threadIdx.x / NT, tid = threadIdx.x % NT;
-    const size_t prod = prod0 + blockIdx.y;
-    const int v0 = blockIdx.x * kNatRows;
-    const Mod md{A.p, A.pp};
-    const size_t tile0 = prod * A.n + static_cast<size_t>(v0);   // u 2^K1 + v0 + t from here
-    // element i of this thread's share of the tile: t = i & 7 (row), u = (i >> 5) + ((i >> 3) & 3) N2 / 4
-    auto row_of = [](int i) { return i & 7; };
-    auto u_of = [](int i) { return (i >> 5) + ((i >> 3) & 3) * (N2 / 4); };
-    if constexpr (INVERSE) {
-        uint32_t v[PER];
-#pragma unroll
-        for (int e = 0; e < PER; e++) {
-            const int i = threadIdx.x + e * THREADS;
-            v[e] = A.src[tile0 + (static_cast<size_t>(u_of(i)) << A.k1) + row_of(i)];
-        }
-#pragma unroll
-        for (int e = 0; e < PER; e++) {
-            const int i = threadIdx.x + e * THREADS;
-            smem[row_of(i) * RW + PadLayout::off(brev_n(u_of(i), K2))] = v[e];
-        }
-        __syncthreads();
-    }
-#pragma unroll 1
-    for (int h = 0; h < kNatRows / kNatTeams; h++) {
-        const int t = team + h * kNatTeams, r = brev_n(v0 + t, A.k1);
-        const PadLayout lay[1] = {{smem + t * RW}};
-        if constexpr (!INVERSE) {
-            stage_in<N2, NT>(lay[0], A.src + prod * A.n + (static_cast<size_t>(r) << K2), tid, true,
-                             [](int k) { return k; });
-            __syncthreads();
-            fwd_passes<K2, NT, 1, false, 0, NP - 1>(lay, tid, A.tw, A.k1, r, md);
-        } else {
-            inv_passes<K2, NT, false, NP - 1, 0>(lay[0], tid, A.tw, A.k1, r, md);
-            uint32_t *g = A.dst + prod * A.n + (static_cast<size_t>(r) << K2);
-            for (int k = tid; k < N2; k += NT) g[k] = lay[0][k];
-        }
-    }
-    if constexpr (!INVERSE) {
-#pragma unroll 4
-        for (int e = 0; e < PER; e++) {
-            const int i = threadIdx.x + e * THREADS;
-            A.dst[tile0 + (static_cast<size_t>(u_of(i)) << A.k1) + row_of(i)] =
-                csub(smem[row_of(i) * RW + PadLayout::off(brev_n(u_of(i), K2))], A.p);
-        }
-    }
-}
-
 __device__ __forceinline__ int brev5(int x)
 {
     return static_cast<int>(__brev(static_cast<unsigned>(x)) >> 27);
@@ -500,21 +411,6 @@ int dispatch_col_itft(int k1, uint32_t rows, const ColArgs &A, size_t count, cud
     }
 }
 
-template <bool INVERSE>
-int launch_row_nat(const RowNatArgs &A, size_t count, cudaStream_t s)
-{
-    constexpr int K2 = 12;
-    const size_t smem = static_cast<size_t>(kNatRows) * nat_row_words<K2>() * sizeof(uint32_t);
-    if (ensure_smem(k_row_ntt_nat<K2, INVERSE>, smem) != MONT_OK) return MONT_ECUDA;
-    const unsigned groups = static_cast<unsigned>((A.n >> K2) / kNatRows);
-    for (size_t first = 0; first < count; first += kMaxGridZ) {
-        const unsigned y = static_cast<unsigned>(std::min<size_t>(kMaxGridZ, count - first));
-        k_row_ntt_nat<K2, INVERSE><<<dim3(groups, y), kNatTeams * nt_of<K2>(), smem, s>>>(A, first);
-        if (cudaGetLastError() != cudaSuccess) return MONT_ECUDA;
-    }
-    return MONT_OK;
-}
-
 int launch_bitrev(uint32_t *data, int log2n, size_t batch, cudaStream_t s)
 {
     if (log2n < 10) return MONT_EUNSUPPORTED;
@@ -591,64 +487,11 @@ int polymul_large(const ntt_plan &plan, const uint32_t *a, size_t la, const uint
     return dispatch_col<true>(k1, I, 1, count, s);
 }
 
-// Natural-order transforms of 2^15 .. 2^22 in two passes: columns (2^K1,
-// K1 = K - 12) and rows of 2^12 written transposed by k_row_ntt_nat, through
-// a library-owned scratch buffer per (device, stream) of at most 1 GiB
-// (larger batches run in chunks).
-constexpr int kNatMinLog = 15, kNatMaxLog = 22, kNatRowLog = 12;
-
-int ntt_large_natural(const ntt_plan *plan, uint32_t *data, size_t batch, bool inverse, cudaStream_t s)
-{
-    const int k = plan->log2n, k2 = kNatRowLog, k1 = k - k2;
-    const size_t n = size_t{1} << k;
-    const size_t per = n * sizeof(uint32_t);
-    const size_t chunk = std::max<size_t>(1, std::min(batch, (size_t{1} << 30) / per));
-    void *wsp = nullptr;
-    int rc = stream_workspace(s, chunk * per, &wsp);
-    if (rc != MONT_OK) return rc;
-    uint32_t *ws = static_cast<uint32_t *>(wsp);
-    for (size_t first = 0; first < batch && rc == MONT_OK; first += chunk) {
-        const size_t cnt = std::min(chunk, batch - first);
-        uint32_t *d = data + first * n;
-        ColArgs C{};
-        C.src_len[0] = C.src_len[1] = n;
-        C.src_stride[0] = C.src_stride[1] = n;
-        C.dst_len = n;
-        C.dst_stride = n;
-        C.k2 = k2;
-        C.p = plan->p;
-        C.pp = plan->p_prime;
-        C.rows = 1u << k1;
-        RowNatArgs R{nullptr, nullptr, n, k1, nullptr, plan->p, plan->p_prime};
-        if (!inverse) {
-            C.src[0] = C.src[1] = d;
-            C.dst[0] = C.dst[1] = ws;
-            C.tw = R.tw = plan->table->fwd;
-            R.src = ws;
-            R.dst = d;
-            rc = dispatch_col<false>(k1, C, 1, cnt, s);
-            if (rc == MONT_OK) rc = launch_row_nat<false>(R, cnt, s);
-        } else {
-            R.src = d;
-            R.dst = ws;
-            C.src[0] = C.src[1] = ws;
-            C.dst[0] = C.dst[1] = d;
-            C.tw = R.tw = plan->table->inv;
-            C.post = plan->ninv_mont;
-            rc = launch_row_nat<true>(R, cnt, s);
-            if (rc == MONT_OK) rc = dispatch_col<true>(k1, C, 1, cnt, s);
-        }
-    }
-    return rc;
-}
-
 int ntt_large(const ntt_plan *plan, uint32_t *data, size_t batch, int flags, bool inverse, cudaStream_t s)
 {
     const int k = plan->log2n, k2 = split_k2(k), k1 = k - k2;
     const size_t n = size_t{1} << k;
     if (batch > SIZE_MAX / n / 4) return MONT_ERANGE;
-    if (!(flags & NTT_BITREV) && k >= kNatMinLog && k <= kNatMaxLog)
-        return ntt_large_natural(plan, data, batch, inverse, s);
     ColArgs C{};
     C.src[0] = C.src[1] = data;
     C.src_len[0] = C.src_len[1] = n;
