@@ -1,5 +1,6 @@
-// polymul_batch.cu -- many products of uneven sizes and mixed primes in ONE
-// persistent kernel launch (optionally replayed as a CUDA graph).
+// polymul_batch.cu -- many products of uneven sizes and mixed primes in one
+// persistent kernel launch, or in the phased form's few kernels (either
+// optionally replayed as a CUDA graph).
 //
 // The host turns the batch into a job list.  A product with N <= 2^13 is
 // computed whole by one team of threads (SMALL job; a job covers as many
@@ -23,6 +24,11 @@
 // so the grid always makes progress.  Each wait is bounded (iterations and
 // elapsed time); on expiry the CTA sets the error word, skips the job and
 // the host reports MONT_ETIMEOUT.
+//
+// Truncated products (Prod::tft) compute only the rows of 2^13 their output
+// reaches and invert each column with an inverse TFT (itft_node).  The
+// phased form (further below) runs the same jobs as one kernel per job kind
+// in stream order, with no waits.
 #include <algorithm>
 #include <map>
 #include <mutex>

@@ -10,9 +10,10 @@
 // memory, reports completions), admits queued requests while the budget
 // allows, and, for every idle slot, launches the admitted requests (up to a
 // coefficient cap) as one batch: copies of the operands into the budget
-// region, one persistent batch kernel (the job-list kernel of
-// polymul_batch.cu, whose builder groups products by padded size), and copies
-// of the results back.  Requests that arrive while batches run are admitted as
+// region, the batch's kernels (the phased form of polymul_batch.cu: one
+// kernel per job kind, the small products on a side stream of the slot;
+// truncated transforms where they save rows), and copies of the results
+// back.  Requests that arrive while batches run are admitted as
 // memory frees up and launched on the next idle slot, so their work overlaps
 // with the batches already on the device.  Each slot has a launcher thread
 // that builds its batch and queues the copies and kernels, so the host work of
