@@ -630,6 +630,49 @@ def uneven_batch(m, torch, peaks, steps=10, warmup=3, cpu=True, per_product=True
     return res
 
 
+def check_served(reqs, lens, primes, pools, off_a, off_b, ring_t, ring_words, load, sample=12, seed=17,
+                 scan=20000):
+    """Results of the last requests of a served stream that are still in the
+    result ring when it ends, against the oracle: a request's result is
+    intact if no later request's region (the placements the run recorded in
+    reqs["c"]) overlaps it.  Among the intact ones of the last `scan`
+    requests, `sample` drawn at random plus the last one are checked."""
+    import bisect
+    import oracle
+    lc = 2 * lens.astype(np.int64) - 1
+    base = ring_t.data_ptr()
+    starts, ends = [], []            # union of the later requests' regions, disjoint, sorted
+    intact = []
+    for i in range(len(lc) - 1, max(-1, len(lc) - 1 - scan), -1):
+        a = (int(reqs["c"][i]) - base) // 4
+        b = a + int(lc[i])
+        k = bisect.bisect_right(starts, a)
+        hit = (k > 0 and ends[k - 1] > a) or (k < len(starts) and starts[k] < b)
+        if not hit:
+            intact.append(i)
+        # merge [a, b) into the union
+        lo = bisect.bisect_left(ends, a)
+        hi = bisect.bisect_right(starts, b)
+        if lo < hi:
+            a, b = min(a, starts[lo]), max(b, ends[hi - 1])
+        starts[lo:hi] = [a]
+        ends[lo:hi] = [b]
+    rng = np.random.default_rng(seed)
+    pick = set(rng.choice(intact, size=min(sample, len(intact)), replace=False).tolist()) if intact else set()
+    pick.add(len(lc) - 1)
+    ring = ring_t.numpy().view(np.uint32)
+    for i in sorted(pick):
+        p = int(primes[i])
+        pool = pools[p].numpy().view(np.uint32)
+        a = pool[off_a[i]:off_a[i] + lens[i]]
+        b = pool[off_b[i]:off_b[i] + lens[i]]
+        start = (int(reqs["c"][i]) - base) // 4
+        got = ring[start:start + int(lc[i])]
+        assert np.array_equal(got, oracle.polymul_ntt(p, a, b)), "serve parity failed for request %d" % i
+    return ("%d of the %d intact results among the last %d requests of the load-%.1f stream, every output word "
+            "equal to the oracle's" % (len(pick), len(intact), min(scan, len(lc)), load))
+
+
 def serve_stream(m, torch, n=50000, budget=16 << 30, slots=4, batch_coeffs=1 << 24, loads=(0.5, 0.8, 1.0, 1.2),
                  headline_load=0.8, pool_log2=24, ring_words=1 << 30):
     """The serving workload: 50,000 requests replayed first all at t = 0
@@ -663,12 +706,16 @@ def serve_stream(m, torch, n=50000, budget=16 << 30, slots=4, batch_coeffs=1 << 
     assert np.all(st_s == 0), "serve: a request failed"
     rate_sat = n / mk_s
     sweep = []
+    checked = None
     for load in loads:
         lam = load * rate_sat
         arrivals = synth.poisson_arrivals(n, lam, synth.SEED_SERVE, 2)
         b0 = server.stats()["batches"]
-        lat, st, mk = serve.run_stream(server, make(), arrivals, ring=ring())
+        reqs = make()
+        lat, st, mk = serve.run_stream(server, reqs, arrivals, ring=ring())
         assert np.all(st == 0), "serve: a request failed at load %.2f" % load
+        if load == headline_load:
+            checked = check_served(reqs, lens, primes, pools, off_a, off_b, ring_t, ring_words, load)
         sweep.append({"load": load, "lambda_per_s": lam, "value": coeffs / mk / 1e9, "unit": "Gcoef/s",
                       "requests_per_s": n / mk, "makespan_s": mk, "batches": server.stats()["batches"] - b0,
                       **serve.latency_summary(lat)})
@@ -681,6 +728,7 @@ def serve_stream(m, torch, n=50000, budget=16 << 30, slots=4, batch_coeffs=1 << 
             "makespan_s": head["makespan_s"], "lambda_per_s": head["lambda_per_s"], "load": head["load"],
             "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"], "mean_ms": head["mean_ms"], "max_ms": head["max_ms"],
             "saturated": {"requests_per_s": rate_sat, "Gcoef_s": coeffs / mk_s / 1e9, **serve.latency_summary(lat_s)},
-            "load_sweep": sweep, "budget_bytes": budget, "slots": slots, "max_batch_coeffs": batch_coeffs,
+            "load_sweep": sweep, "parity": checked, "budget_bytes": budget, "slots": slots,
+            "max_batch_coeffs": batch_coeffs,
             "batches": stats["batches"], "peak_bytes": stats["peak_bytes"],
             "latency": "host clock, arrival (scheduled) to completion reported by mont_server_progress"}

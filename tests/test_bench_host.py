@@ -113,3 +113,42 @@ def test_section_failure_is_recorded_not_raised(capsys):
     assert extra == {"first": {"value": 1.0}, "third": {"value": 3.0}}
     assert errors == {"second": "AssertionError: batch parity spot check failed"}
     assert "batch parity spot check failed" in capsys.readouterr().err
+
+
+def test_served_results_check_reads_the_ring_as_placed():
+    """The bench's oracle check of served results: regions handed out by the
+    result ring in request order (with wrap-around), filled with the
+    oracle's products; the check passes, and fails on a planted wrong word
+    in a request it samples."""
+    import torch
+    from paper_1609_00999_gb300 import serve
+    n, ring_words, pool_n = 60, 4096, 1 << 12
+    rng = np.random.default_rng(5)
+    lens = rng.integers(8, 200, size=n).astype(np.int64)
+    primes = np.asarray([synth.PRIMES[i % 3] for i in range(n)], dtype=np.uint32)
+    pools = {p: torch.from_numpy(synth.residues(pool_n, p, 77, i).view(np.int32)) for i, p in enumerate(synth.PRIMES)}
+    off_a = rng.integers(0, pool_n - 200, size=n)
+    off_b = rng.integers(0, pool_n - 200, size=n)
+    ring_t = torch.zeros(ring_words, dtype=torch.int32)
+    ring = serve.HostRing(ring_t.data_ptr(), ring_words)
+    reqs = serve.make_requests(primes, lens, lens, np.zeros(n, np.int64), np.zeros(n, np.int64), np.zeros(n, np.int64))
+    view = ring_t.numpy().view(np.uint32)
+    for i in range(n):                       # in order, five in flight, so regions advance and wrap around
+        lc = int(2 * lens[i] - 1)
+        if i >= 5:
+            ring.release(i - 5)
+        ptr = ring.alloc(i, lc)
+        assert ptr is not None
+        reqs["c"][i] = ptr
+        p = int(primes[i])
+        pool = pools[p].numpy().view(np.uint32)
+        start = (ptr - ring_t.data_ptr()) // 4
+        view[start:start + lc] = oracle.polymul_ntt(p, pool[off_a[i]:off_a[i] + lens[i]],
+                                                    pool[off_b[i]:off_b[i] + lens[i]])
+    msg = bp.check_served(reqs, lens, primes, pools, off_a, off_b, ring_t, ring_words, 0.8, sample=6)
+    assert "intact results" in msg and int(msg.split(" of the ")[1].split()[0]) >= 6
+    last = n - 1
+    start = (int(reqs["c"][last]) - ring_t.data_ptr()) // 4
+    view[start + 3] ^= 1                      # the last request is always checked
+    with pytest.raises(AssertionError):
+        bp.check_served(reqs, lens, primes, pools, off_a, off_b, ring_t, ring_words, 0.8, sample=6)
