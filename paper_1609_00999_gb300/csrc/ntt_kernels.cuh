@@ -117,7 +117,8 @@ struct PlainLoad {
     __device__ __forceinline__ uint32_t operator()(int arr, int j) const
     {
         const uint32_t *g = arr ? b : a;
-        const uint32_t v = j < (arr ? lb : la) ? load_operand<READ_ONLY>(g + j) : 0u;
+        if (j >= (arr ? lb : la)) return 0u;   // zero padding: no load, no scaling
+        const uint32_t v = load_operand<READ_ONLY>(g + j);
         return (SCALE_B && arr) ? RED::mul(v, k_scale, m) : v;
     }
 };
