@@ -343,13 +343,14 @@ int polymul_batch_status(polymul_batch_plan *plan, cudaStream_t stream);
  * last run. */
 int polymul_batch_plan_tune(polymul_batch_plan *plan, cudaStream_t stream, int trials);
 
-/* One-shot batch without a plan: the same persistent kernel and results as
- * polymul_batch_plan_create + polymul_batch_run, in a fixed launch shape
- * (the 3-CTA/SM register budget, job order 0), with every device table of
- * the batch in the caller's workspace.  Each call validates the
- * descriptors, builds the job list on the host, queues copies of it and of
- * the product table from pageable host memory into the workspace (so not
- * during stream capture; a plan can be captured), and launches the kernel.
+/* One-shot batch without a plan: the same kernels and results as
+ * polymul_batch_plan_create + polymul_batch_run, in the phased form with
+ * truncated transforms (every kernel in order on `stream`), with every
+ * device table of the batch in the caller's workspace.  Each call validates
+ * the descriptors, builds the job lists on the host, queues copies of them
+ * and of the product table from pageable host memory into the workspace (so
+ * not during stream capture; a plan can be captured), and launches the
+ * kernels.
  * workspace: device memory, 256-byte aligned (as cudaMalloc returns), at
  * least polymul_batch_workspace_bytes(descs, count) bytes; it must not be
  * used by other work until the queued kernel finishes (calls on one stream
@@ -360,12 +361,14 @@ int polymul_batch_plan_tune(polymul_batch_plan *plan, cudaStream_t stream, int t
 int polymul_batch(const polymul_desc *descs, size_t count, void *workspace, size_t ws_bytes, cudaStream_t stream);
 
 /* Host only: workspace bytes polymul_batch needs for these descriptors
- * (counters, product table, job list and 2N words of scratch per product
- * with N > 2^13); 0 for count == 0 or invalid descriptors. */
+ * (counters, product table, the phased form's job lists and 2N words of
+ * scratch per product with N > 2^13); 0 for count == 0 or invalid
+ * descriptors. */
 size_t polymul_batch_workspace_bytes(const polymul_desc *descs, size_t count);
 
-/* Synchronises `stream`, then reports MONT_OK, or MONT_ETIMEOUT when a
- * bounded wait inside the last polymul_batch run on this workspace expired. */
+/* Synchronises `stream`, then reports the status word of the last
+ * polymul_batch run on this workspace: MONT_OK (the phased form has no
+ * device-side waits, so nothing sets MONT_ETIMEOUT there). */
 int polymul_batch_check(const void *workspace, cudaStream_t stream);
 
 /* Bound of every device-side wait of the plan (default 2^22 polls, 2 s). */

@@ -90,8 +90,9 @@ int batch_launch(BatchArgs A, const Job *jobs, uint32_t njobs, size_t sync_words
                  cudaStream_t s);
 // The phased form: the batch's jobs split by kind, each kind its own kernel
 // (one CTA per job), ordered by stream dependencies: the small products on a
-// side stream forked from s and joined back, every larger product's forward
-// columns, rows and output tiles on s.
+// side stream forked from s and joined back (aux null or s: all on s, fork
+// and join unused), every larger product's forward columns, rows and output
+// tiles on s.
 enum PhaseList { PH_COLF_REG = 0, PH_COLF_TILE, PH_ROW, PH_COLI_REG, PH_COLI_TILE, PH_LISTS };
 
 struct PhasedHost {

@@ -1,11 +1,12 @@
 // batch_oneshot.cu -- polymul_batch: one uneven batch without a plan, every
 // device-side table of the batch in the caller's workspace.
 //
-// The same persistent kernel and job list as a batch plan (polymul_batch.cu),
-// in the configuration the request server runs (the 3-CTA/SM register
-// budget, column tiles first).  Each call builds the job list on the host
-// and queues copies of it and of the product table into the workspace; a
-// plan does that once, and can also be tuned and replayed as a CUDA graph.
+// The same kernels as a batch plan (polymul_batch.cu) in the form the tuner
+// picks for uneven batches and the request server runs: the phased form, one
+// kernel per job kind, here all in order on the caller's stream, with
+// truncated transforms.  Each call builds the job lists on the host and
+// queues copies of them and of the product table into the workspace; a plan
+// does that once, and can also be tuned and replayed as a CUDA graph.
 #include <algorithm>
 #include <vector>
 
@@ -16,8 +17,6 @@ namespace mont {
 namespace {
 
 constexpr size_t kPart = 256;          // every part of the workspace starts 256-byte aligned
-constexpr int kOneShotOrder = 0;       // column tiles, whole and small products, rows, output tiles
-constexpr int kOneShotVariant = 1;     // registers budgeted for three CTAs per SM
 
 size_t round_up(size_t x)
 {
@@ -25,18 +24,19 @@ size_t round_up(size_t x)
 }
 
 // Byte offsets of the workspace parts: the counters (2 + 2 count words), the
-// product table, the job list, then the split products' scratch.
+// product table, the phased form's job lists, then the split products'
+// scratch.
 struct Layout {
     size_t sync, prods, jobs, scratch, total;
 };
 
-Layout layout_of(const BatchHost &h, size_t count)
+Layout layout_of(const BatchHost &h, const PhasedHost &ph, size_t count)
 {
     Layout L;
     L.sync = 0;
     L.prods = round_up((2 + 2 * count) * sizeof(uint32_t));
     L.jobs = L.prods + round_up(count * sizeof(Prod));
-    L.scratch = L.jobs + round_up(h.jobs[kOneShotOrder].size() * sizeof(Job));
+    L.scratch = L.jobs + round_up(ph.jobs.size() * sizeof(Job));
     L.total = L.scratch + h.ws_words * sizeof(uint32_t);
     return L;
 }
@@ -57,10 +57,12 @@ extern "C" size_t polymul_batch_workspace_bytes(const polymul_desc *descs, size_
     using namespace mont;
     if (count == 0) return 0;
     BatchHost h;
+    PhasedHost ph;
     std::vector<uint32_t> primes;
     std::vector<int> logs;
     if (build(descs, count, h, primes, logs) != MONT_OK) return 0;
-    return layout_of(h, count).total;
+    phased_build(h, ph);
+    return layout_of(h, ph, count).total;
 }
 
 extern "C" int polymul_batch(const polymul_desc *descs, size_t count, void *workspace, size_t ws_bytes,
@@ -69,11 +71,13 @@ extern "C" int polymul_batch(const polymul_desc *descs, size_t count, void *work
     using namespace mont;
     if (count == 0) return MONT_OK;
     BatchHost h;
+    PhasedHost ph;
     std::vector<uint32_t> primes;
     std::vector<int> logs;
     int rc = build(descs, count, h, primes, logs);
     if (rc != MONT_OK) return rc;
-    const Layout L = layout_of(h, count);
+    phased_build(h, ph);
+    const Layout L = layout_of(h, ph, count);
     if (!workspace || (reinterpret_cast<uintptr_t>(workspace) % kPart) != 0 || ws_bytes < L.total)
         return MONT_EINVAL;
 
@@ -84,16 +88,11 @@ extern "C" int polymul_batch(const polymul_desc *descs, size_t count, void *work
         if (rc != MONT_OK) return rc;
         A.primes[i] = PrimeInfo{t->p, t->p_prime, t->fwd, t->inv};
     }
-    int occ = 0;
-    if (batch_occupancy(kOneShotVariant, &occ) != MONT_OK) return MONT_ECUDA;
-    const int sms = device_sm_count();
-    if (sms <= 0) return MONT_ECUDA;
-
     uint8_t *base = static_cast<uint8_t *>(workspace);
     batch_rebase(h, reinterpret_cast<uint32_t *>(base + L.scratch));
     Prod *d_prods = reinterpret_cast<Prod *>(base + L.prods);
     Job *d_jobs = reinterpret_cast<Job *>(base + L.jobs);
-    const std::vector<Job> &jobs = h.jobs[kOneShotOrder];
+    const std::vector<Job> &jobs = ph.jobs;
     // Copies from pageable memory return once the data is staged, so the
     // host tables may go out of scope before the copies reach the device.
     if (cudaMemcpyAsync(d_prods, h.prods.data(), count * sizeof(Prod), cudaMemcpyHostToDevice, stream) !=
@@ -107,8 +106,7 @@ extern "C" int polymul_batch(const polymul_desc *descs, size_t count, void *work
     A.sync = reinterpret_cast<uint32_t *>(base + L.sync);
     A.wait_iters = 1u << 22;
     A.wait_ns = 2000000000ull;   // 2 s per wait
-    return batch_launch(A, d_jobs, static_cast<uint32_t>(jobs.size()), 2 + 2 * count, sms * occ, kOneShotVariant,
-                        stream);
+    return batch_launch_phased(A, ph, d_jobs, 2 + 2 * count, stream, nullptr, nullptr, nullptr);
 }
 
 // Synchronous: waits for `stream`, then reads the error word (word 1 of the

@@ -894,7 +894,9 @@ int batch_launch_phased(BatchArgs A, const PhasedHost &ph, const Job *d_jobs, si
                         cudaStream_t aux, cudaEvent_t fork, cudaEvent_t join)
 {
     if (cudaMemsetAsync(A.sync, 0, sync_words * sizeof(uint32_t), s) != cudaSuccess) return MONT_ECUDA;
-    if (cudaEventRecord(fork, s) != cudaSuccess || cudaStreamWaitEvent(aux, fork, 0) != cudaSuccess)
+    const bool side = aux != nullptr && aux != s;   // else every kernel in order on s
+    if (!side) aux = s;
+    else if (cudaEventRecord(fork, s) != cudaSuccess || cudaStreamWaitEvent(aux, fork, 0) != cudaSuccess)
         return MONT_ECUDA;
     int rc = MONT_OK;
     for (size_t i = 0; i + 2 < ph.small.size() && rc == MONT_OK; i += 3)
@@ -908,7 +910,7 @@ int batch_launch_phased(BatchArgs A, const PhasedHost &ph, const Job *d_jobs, si
     if (rc == MONT_OK) rc = phase_jobs(k_phase_col_tile<true>, A, list(PH_COLI_TILE), ph.cnt[PH_COLI_TILE], smem, s);
     // Join the side branch back into s (also after a failed launch, so no
     // branch is left open in a capture).
-    const bool joined = cudaEventRecord(join, aux) == cudaSuccess && cudaStreamWaitEvent(s, join, 0) == cudaSuccess;
+    const bool joined = !side || (cudaEventRecord(join, aux) == cudaSuccess && cudaStreamWaitEvent(s, join, 0) == cudaSuccess);
     return rc != MONT_OK ? rc : (joined ? MONT_OK : MONT_ECUDA);
 }
 

@@ -172,22 +172,25 @@ def test_describe_rejects_bad_input(m):
 
 def test_one_shot_workspace_layout(m):
     """polymul_batch's workspace: counters (2 + 2 count words), product table
-    (64 B per product), job list of order 0 (16 B per job, truncated
-    transforms on), each part rounded
-    up to 256 B, then 2N words of scratch per product with N > 2^13."""
+    (64 B per product), the phased form's job lists (16 B per job: the
+    column, row and output-tile jobs of every product above 2^13, truncated
+    transforms on), each part rounded up to 256 B, then 2N words of scratch
+    per product with N > 2^13."""
     def up(x):
         return (x + 255) // 256 * 256
 
     lens = synth.loguniform_lengths(400, 1 << 4, 1 << 17, 4321, 0)
     primes = synth.choose_primes(400, 4321, 1)
     descs = fake_descs(m, lens, lens, primes)
-    jobs, _ = m.polymul_batch_describe(descs, 0)
+    jobs, prods = m.polymul_batch_describe(descs, 0)
+    njobs = sum(1 for j in jobs.tolist() if j[0] in (COLF, ROW, COLI))
+    njobs += sum(2 * int(prods[j[2]][1]) + int(prods[j[2]][2]) for j in jobs.tolist() if j[0] == WHOLE)
     scratch = 0
     for L in lens:
         n = 1 << int(2 * int(L) - 2).bit_length()
         if n > 1 << 13:
             scratch += 2 * n
-    want = up(4 * (2 + 2 * len(descs))) + up(64 * len(descs)) + up(16 * len(jobs)) + 4 * scratch
+    want = up(4 * (2 + 2 * len(descs))) + up(64 * len(descs)) + up(16 * njobs) + 4 * scratch
     assert m.polymul_batch_workspace_bytes(descs) == want
 
 
