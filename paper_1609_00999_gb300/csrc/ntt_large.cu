@@ -10,13 +10,18 @@
 // is entry 2^(K1+l) + (r << l) + i.
 //
 // Column kernels: up to four levels in registers, straight from and to
-// global memory (k_col_regs); more levels through a shared-memory tile of C
-// consecutive columns loaded with coalesced row segments, one team of
-// threads per column (k_col).  Row kernel: one CTA per row, the same
-// register passes as the single-CTA kernels.  Forward values between the
+// global memory (k_col_regs); five to eight levels as two register passes
+// over a tile of 32 or more consecutive columns, the first loading from and
+// the second storing to global memory, with one exchange through shared
+// memory between them (k_col_direct); more levels through a shared-memory
+// tile loaded with coalesced row segments, one team of threads per column
+// (k_col).  Row kernel: one CTA per row, the same register passes as the
+// single-CTA kernels, its first pass loading from (forward) or its last pass
+// storing to (inverse) global memory.  Forward values between the
 // column and row kernels are lazy ([0, 2P), as inside the passes); the row
 // kernels take them as such and reduce what they finally store.
 #include <algorithm>
+#include <type_traits>
 
 #include "ntt_kernels.cuh"
 
@@ -103,6 +108,79 @@ k_col(ColArgs A, size_t prod0)
         uint32_t v = mine[t0 + u * S];
         if (A.post) v = mont_mul(v, A.post, p, pp);
         if (static_cast<long long>(u * step) < room_out) dst[first + u * step] = v;
+    }
+}
+
+// Column tiles for K1 = 5 .. 8 (two passes of at most four levels, 16
+// elements per thread, C >= 32 columns per CTA).  The pass that starts the
+// transform loads its elements straight from global memory and the pass
+// that ends it stores them straight back, so only the exchange between the
+// two passes goes through shared memory.  Thread x takes column c = x % C
+// and team position tid = x / C: every access of a warp is one row of 32
+// consecutive columns, a 128-byte segment in global memory, and with column
+// c at word c * (N1 + 1) thirty-two distinct banks in shared memory (each
+// element a per-group pointer plus a compile-time offset).
+template <int K1, bool INVERSE>
+__global__ void __launch_bounds__(ColCfg<K1>::THREADS)
+k_col_direct(ColArgs A, size_t prod0)
+{
+    using CF = ColCfg<K1>;
+    constexpr int NT = CF::NT1;
+    static_assert(SchedFor<K1, NT>::kPasses == 2 && CF::C % 32 == 0, "two passes, whole-warp rows");
+    using P0 = PassGeom<K1, NT, 0>;
+    using P1 = PassGeom<K1, NT, 1>;
+    using PIN = std::conditional_t<INVERSE, P1, P0>;    // the pass that reads global memory
+    using POUT = std::conditional_t<INVERSE, P0, P1>;   // the pass that writes it
+    extern __shared__ __align__(16) uint32_t smem[];
+    const bool op1 = blockIdx.y != 0;
+    const size_t prod = prod0 + blockIdx.z;
+    const uint32_t *src = (op1 ? A.src[1] : A.src[0]) + prod * (op1 ? A.src_stride[1] : A.src_stride[0]);
+    const size_t slen = op1 ? A.src_len[1] : A.src_len[0];
+    uint32_t *dst = (op1 ? A.dst[1] : A.dst[0]) + prod * A.dst_stride;
+    const uint32_t scale = op1 ? A.scale[1] : A.scale[0];
+    const int c = threadIdx.x % CF::C, tid = threadIdx.x / CF::C;
+    const size_t col = static_cast<size_t>(blockIdx.x) * CF::C + c;
+    uint32_t *mine = smem + c * (CF::N1 + 1);
+    const Mod m{A.p, A.pp};
+
+    uint32_t x[PIN::GPT][1][PIN::G];
+    const long long room_in = static_cast<long long>(slen) - static_cast<long long>(col);
+#pragma unroll
+    for (int r = 0; r < PIN::GPT; r++)
+#pragma unroll
+        for (int t = 0; t < PIN::G; t++) {
+            const long long off = static_cast<long long>(PIN::base(tid, r) + t * PIN::HMIN) << A.k2;
+            x[r][0][t] = off < room_in ? __ldg(src + col + off) : 0u;
+        }
+#pragma unroll
+    for (int r = 0; r < PIN::GPT; r++) {
+        if (scale) {
+#pragma unroll
+            for (int t = 0; t < PIN::G; t++) x[r][0][t] = mont_mul(x[r][0][t], scale, m.p, m.pp);
+        }
+        if constexpr (!INVERSE) ct_group<P0::E, 1, true>(x[r], A.tw, 0, 0, m);
+        else gs_group<P1::E, 1, false>(x[r], A.tw, P1::S0, P1::blk(tid, r), m);
+        uint32_t *g = mine + PIN::base(tid, r);
+#pragma unroll
+        for (int t = 0; t < PIN::G; t++) g[t * PIN::HMIN] = x[r][0][t];
+    }
+    __syncthreads();
+    const long long room_out = static_cast<long long>(A.dst_len) - static_cast<long long>(col);
+#pragma unroll
+    for (int r = 0; r < POUT::GPT; r++) {
+        uint32_t y[1][POUT::G];
+        const uint32_t *g = mine + POUT::base(tid, r);
+#pragma unroll
+        for (int t = 0; t < POUT::G; t++) y[0][t] = g[t * POUT::HMIN];
+        if constexpr (!INVERSE) ct_group<P1::E, 1, false>(y, A.tw, P1::S0, P1::blk(tid, r), m);
+        else gs_group<P0::E, 1, true>(y, A.tw, 0, 0, m);
+#pragma unroll
+        for (int t = 0; t < POUT::G; t++) {
+            uint32_t v = y[0][t];
+            if (A.post) v = mont_mul(v, A.post, m.p, m.pp);
+            const long long off = static_cast<long long>(POUT::base(tid, r) + t * POUT::HMIN) << A.k2;
+            if (off < room_out) dst[col + off] = v;
+        }
     }
 }
 
@@ -224,11 +302,40 @@ k_row_ntt(RowNttArgs A, size_t prod0)
     const int r = blockIdx.x;
     uint32_t *g = A.data + prod * A.n + (static_cast<size_t>(r) << K2);
     const PadLayout lay[1] = {{smem}};
-    stage_in<N2, NT>(lay[0], g, threadIdx.x, true, [](int k) { return k; });
-    __syncthreads();
-    if constexpr (!INVERSE) fwd_passes<K2, NT, 1, false, 0, NP - 1>(lay, threadIdx.x, A.tw, A.k1, r, Mod{A.p, A.pp});
-    else inv_passes<K2, NT, false, NP - 1, 0>(lay[0], threadIdx.x, A.tw, A.k1, r, Mod{A.p, A.pp});
-    for (int k = threadIdx.x; k < N2; k += NT) g[k] = INVERSE ? lay[0][k] : csub(lay[0][k], A.p);
+    const Mod md{A.p, A.pp};
+    using P0 = PassGeom<K2, NT, 0>;
+    static_assert(NP >= 2, "rows take at least two passes");
+    if constexpr (!INVERSE) {
+        // pass 0 straight from global memory (a warp reads consecutive words)
+#pragma unroll
+        for (int q = 0; q < P0::GPT; q++) {
+            const int base = P0::base(threadIdx.x, q);
+            uint32_t x[1][P0::G];
+#pragma unroll
+            for (int t = 0; t < P0::G; t++) x[0][t] = g[base + t * P0::HMIN];
+            ct_group<P0::E, 1, false>(x, A.tw, A.k1, (r << P0::S0) + P0::blk(threadIdx.x, q), md);
+#pragma unroll
+            for (int t = 0; t < P0::G; t++) elem(lay[0], base, t * P0::HMIN) = x[0][t];
+        }
+        __syncthreads();
+        fwd_passes<K2, NT, 1, false, 1, NP - 1>(lay, threadIdx.x, A.tw, A.k1, r, md);
+        for (int k = threadIdx.x; k < N2; k += NT) g[k] = csub(lay[0][k], A.p);
+    } else {
+        stage_in<N2, NT>(lay[0], g, threadIdx.x, true, [](int k) { return k; });
+        __syncthreads();
+        inv_passes<K2, NT, false, NP - 1, 1>(lay[0], threadIdx.x, A.tw, A.k1, r, md);
+        // pass 0 straight to global memory
+#pragma unroll
+        for (int q = 0; q < P0::GPT; q++) {
+            const int base = P0::base(threadIdx.x, q);
+            uint32_t x[1][P0::G];
+#pragma unroll
+            for (int t = 0; t < P0::G; t++) x[0][t] = elem(lay[0], base, t * P0::HMIN);
+            gs_group<P0::E, 1, false>(x, A.tw, A.k1, (r << P0::S0) + P0::blk(threadIdx.x, q), md);
+#pragma unroll
+            for (int t = 0; t < P0::G; t++) g[base + t * P0::HMIN] = x[0][t];
+        }
+    }
 }
 
 __device__ __forceinline__ int brev5(int x)
@@ -275,12 +382,17 @@ template <int K1, bool INVERSE>
 int launch_col(const ColArgs &A, size_t nops, size_t count, cudaStream_t s)
 {
     using CF = ColCfg<K1>;
-    if (ensure_smem(k_col<K1, INVERSE>, CF::SMEM) != MONT_OK) return MONT_ECUDA;
+    constexpr bool kDirect = CF::C % 32 == 0 && SchedFor<K1, CF::NT1>::kPasses == 2;
+    constexpr size_t smem = kDirect ? static_cast<size_t>(CF::C) * (CF::N1 + 1) * sizeof(uint32_t) : CF::SMEM;
+    void (*kern)(ColArgs, size_t);
+    if constexpr (kDirect) kern = k_col_direct<K1, INVERSE>;
+    else kern = k_col<K1, INVERSE>;
+    if (ensure_smem(kern, smem) != MONT_OK) return MONT_ECUDA;
     const size_t n2 = size_t{1} << A.k2;
     for (size_t first = 0; first < count; first += kMaxGridZ) {
         const unsigned z = static_cast<unsigned>(std::min<size_t>(kMaxGridZ, count - first));
         dim3 grid(static_cast<unsigned>(n2 / CF::C), static_cast<unsigned>(nops), z);
-        k_col<K1, INVERSE><<<grid, CF::THREADS, CF::SMEM, s>>>(A, first);
+        kern<<<grid, CF::THREADS, smem, s>>>(A, first);
         if (cudaGetLastError() != cudaSuccess) return MONT_ECUDA;
     }
     return MONT_OK;

@@ -55,7 +55,8 @@ def test_large_ntt(m, p, logn):
 
 @pytest.mark.parametrize("p,la,lb", [(synth.P1, 8193, 8192), (synth.P1, 16384, 16385), (synth.P2, 30000, 20000),
                                      (synth.P3, 65536, 65536), (synth.P1, 100000, 31073), (synth.P2, 1, 40000),
-                                     (synth.P1, 1 << 20, 1 << 20), (synth.P3, 700000, 123457)])
+                                     (synth.P1, 1 << 20, 1 << 20), (synth.P3, 700000, 123457),
+                                     (synth.P2, 300000, 100001)])
 def test_large_polymul(m, p, la, lb):
     a = synth.residues(la, p, 401, la, lb, 0)
     b = synth.residues(lb, p, 401, la, lb, 1)
@@ -77,12 +78,14 @@ def test_large_extreme_inputs(m, p):
     b = np.full(lb, p - 1, dtype=np.uint32)
     got = to_host(m.polymul(p, to_dev(a), to_dev(b)))
     assert np.array_equal(got, oracle.polymul_ntt(p, a, b))
-    logn = 16
-    x = np.full((1, 1 << logn), p - 1, dtype=np.uint32)
-    plan = m.ntt_plan_create(p, logn)
-    d = to_dev(x)
-    m.ntt_fwd(plan, d)
-    assert np.array_equal(to_host(d).reshape(1, -1), np.stack([oracle.ntt(p, x[0])]))
+    for logn in (16, 20):                         # register and shared-memory column passes
+        x = np.full((1, 1 << logn), p - 1, dtype=np.uint32)
+        plan = m.ntt_plan_create(p, logn)
+        d = to_dev(x)
+        m.ntt_fwd(plan, d)
+        assert np.array_equal(to_host(d).reshape(1, -1), np.stack([oracle.ntt(p, x[0])]))
+        m.ntt_inv(plan, d)
+        assert np.array_equal(to_host(d).reshape(1, -1), x)
 
 
 def test_large_polymul_many_and_chunked_workspace(m):
