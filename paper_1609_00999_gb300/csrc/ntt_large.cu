@@ -121,7 +121,7 @@ k_col(ColArgs A, size_t prod0)
 // c at word c * (N1 + 1) thirty-two distinct banks in shared memory (each
 // element a per-group pointer plus a compile-time offset).
 template <int K1, bool INVERSE>
-__global__ void __launch_bounds__(ColCfg<K1>::THREADS)
+__global__ void __launch_bounds__(ColCfg<K1>::THREADS, 3)
 k_col_direct(ColArgs A, size_t prod0)
 {
     using CF = ColCfg<K1>;
@@ -143,15 +143,28 @@ k_col_direct(ColArgs A, size_t prod0)
     uint32_t *mine = smem + c * (CF::N1 + 1);
     const Mod m{A.p, A.pp};
 
+    // Row j of this column is element col + j 2^k2 (< 2^24, so 32-bit
+    // offsets); rows_below(len) counts the rows j with that index below len.
+    const int k2 = A.k2;
+    auto rows_below = [&](size_t len) -> int {
+        if (len <= col) return 0;
+        const size_t rows = (len - col + (size_t{1} << k2) - 1) >> k2;
+        return rows < static_cast<size_t>(CF::N1) ? static_cast<int>(rows) : CF::N1;
+    };
     uint32_t x[PIN::GPT][1][PIN::G];
-    const long long room_in = static_cast<long long>(slen) - static_cast<long long>(col);
+    {
+        const int rows_in = rows_below(slen);
+        const uint32_t *sc = src + col;
+        const uint32_t hs = static_cast<uint32_t>(PIN::HMIN) << k2;
 #pragma unroll
-    for (int r = 0; r < PIN::GPT; r++)
+        for (int r = 0; r < PIN::GPT; r++) {
+            const int j0 = PIN::base(tid, r);
+            const uint32_t e0 = static_cast<uint32_t>(j0) << k2;
 #pragma unroll
-        for (int t = 0; t < PIN::G; t++) {
-            const long long off = static_cast<long long>(PIN::base(tid, r) + t * PIN::HMIN) << A.k2;
-            x[r][0][t] = off < room_in ? __ldg(src + col + off) : 0u;
+            for (int t = 0; t < PIN::G; t++)
+                x[r][0][t] = j0 + t * PIN::HMIN < rows_in ? __ldg(sc + (e0 + t * hs)) : 0u;
         }
+    }
 #pragma unroll
     for (int r = 0; r < PIN::GPT; r++) {
         if (scale) {
@@ -165,7 +178,9 @@ k_col_direct(ColArgs A, size_t prod0)
         for (int t = 0; t < PIN::G; t++) g[t * PIN::HMIN] = x[r][0][t];
     }
     __syncthreads();
-    const long long room_out = static_cast<long long>(A.dst_len) - static_cast<long long>(col);
+    const int rows_out = rows_below(A.dst_len);
+    uint32_t *dc = dst + col;
+    const uint32_t hs_out = static_cast<uint32_t>(POUT::HMIN) << k2;
 #pragma unroll
     for (int r = 0; r < POUT::GPT; r++) {
         uint32_t y[1][POUT::G];
@@ -178,8 +193,8 @@ k_col_direct(ColArgs A, size_t prod0)
         for (int t = 0; t < POUT::G; t++) {
             uint32_t v = y[0][t];
             if (A.post) v = mont_mul(v, A.post, m.p, m.pp);
-            const long long off = static_cast<long long>(POUT::base(tid, r) + t * POUT::HMIN) << A.k2;
-            if (off < room_out) dst[col + off] = v;
+            const int j0 = POUT::base(tid, r);
+            if (j0 + t * POUT::HMIN < rows_out) dc[(static_cast<uint32_t>(j0) << k2) + t * hs_out] = v;
         }
     }
 }
@@ -293,7 +308,7 @@ struct RowNttArgs {
 };
 
 template <int K2, bool INVERSE>
-__global__ void __launch_bounds__(nt_of<K2>())
+__global__ void __launch_bounds__(nt_of<K2>(), K2 <= 13 ? 4 : 1)
 k_row_ntt(RowNttArgs A, size_t prod0)
 {
     constexpr int N2 = 1 << K2, NT = nt_of<K2>(), NP = SchedFor<K2, NT>::kPasses;
@@ -451,6 +466,15 @@ int split_k2(int k)
     return std::max(13, k - 10);
 }
 
+// Products of N = 2^19 and 2^20 take rows of 2^12 (the fused 4096-point row
+// product, four CTAs per SM, after seven or eight column levels): 18 % and
+// 11 % faster than rows of 2^13, while 2^21 is faster with rows of 2^13 and
+// the stand-alone transforms keep rows of 2^13.
+int split_k2_polymul(int k)
+{
+    return (k == 19 || k == 20) ? 12 : split_k2(k);
+}
+
 #define MONT_K1_TILE_CASES(X) X(5) X(6) X(7) X(8) X(9) X(10)
 
 template <bool INVERSE>
@@ -540,7 +564,7 @@ int launch_bitrev(uint32_t *data, int log2n, size_t batch, cudaStream_t s)
 int polymul_large(const ntt_plan &plan, const uint32_t *a, size_t la, const uint32_t *b, size_t lb, uint32_t *c,
                   size_t count, uint32_t *ws, cudaStream_t s)
 {
-    const int k = plan.log2n, k2 = split_k2(k), k1 = k - k2;
+    const int k = plan.log2n, k2 = split_k2_polymul(k), k1 = k - k2;
     const size_t n = size_t{1} << k;
     // Row-granular truncated transform (as in the batches): with register
     // column passes (2 <= K1 <= 4), compute only the ceil(lc / 2^K2) rows the
