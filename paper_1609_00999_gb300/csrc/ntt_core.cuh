@@ -232,8 +232,17 @@ template <int LOGN, int NT>
 using SchedFor = Sched<LOGN, (LOGN - ilog2(NT) >= 5 ? 5 : 4)>;
 
 // Geometry of pass I of a 2^LOGN sub-transform processed by NT threads, each
-// holding EPT = 2^LOGN / NT elements per array (EPT / 2^E groups).
-template <int LOGN, int NT, int I>
+// holding EPT = 2^LOGN / NT elements per array (EPT / 2^E groups).  Group q
+// (of NT * GPT) starts at element ((q / HMIN) << (LOGN - S0)) + q % HMIN;
+// thread tid takes groups grp(tid) + NT r.
+//
+// PADDED (the PadLayout, one padding word per 32): a warp whose lanes run
+// over 32 / HMIN blocks of HMIN * G words sees block b's words shifted by
+// b * HMIN * G / 32 banks, so with G = 16 and HMIN = 8 or 16 (the middle
+// passes of 2^11 .. 2^13) consecutive blocks overlap: 2-way conflicts.
+// grp then hands the warp's HMIN-lane segments blocks D = 32 / G apart,
+// shifting each segment by HMIN banks, and the warp covers 32 banks.
+template <int LOGN, int NT, int I, bool PADDED = false>
 struct PassGeom {
     static constexpr int S0 = SchedFor<LOGN, NT>::start(I);
     static constexpr int E = SchedFor<LOGN, NT>::levels(I);
@@ -242,11 +251,25 @@ struct PassGeom {
     static constexpr int HMIN = 1 << LOG_HMIN;
     static constexpr int GPT = (1 << LOGN) / G / NT;
     static_assert(GPT >= 1, "too many threads for this sub-transform");
+    static constexpr int D = G < 32 ? 32 / G : 1;
+    static constexpr bool REMAP =
+        PADDED && HMIN >= 2 && HMIN < 32 && G < 32 && HMIN * G >= 32 && NT % (32 * D) == 0;
+    __device__ __forceinline__ static int grp(int tid)
+    {
+        if constexpr (!REMAP) {
+            return tid;
+        } else {
+            constexpr int NB = 32 / HMIN;   // blocks one warp touches
+            const int w = tid >> 5, l = tid & 31;
+            const int block = (w / D) * (D * NB) + (w % D) + (l / HMIN) * D;
+            return block * HMIN + (l % HMIN);
+        }
+    }
     // block index (at level S0) and first element of group r of thread tid
-    __device__ __forceinline__ static int blk(int tid, int r) { return (tid + NT * r) >> LOG_HMIN; }
+    __device__ __forceinline__ static int blk(int tid, int r) { return (grp(tid) + NT * r) >> LOG_HMIN; }
     __device__ __forceinline__ static int base(int tid, int r)
     {
-        const int q = tid + NT * r;
+        const int q = grp(tid) + NT * r;
         return ((q >> LOG_HMIN) << (LOGN - S0)) + (q & (HMIN - 1));
     }
 };
@@ -312,7 +335,7 @@ template <int LOGN, int NT, int I, int NARR, bool BASE0, class RED = RedAlg2, cl
 __device__ __forceinline__ void fwd_pass(const L (&lay)[NARR], int tid, const uint32_t *__restrict__ tw, int s_base,
                                          int b, Mod m)
 {
-    using PG = PassGeom<LOGN, NT, I>;
+    using PG = PassGeom<LOGN, NT, I, L::kAdditive>;
 #pragma unroll
     for (int a = 0; a < NARR; a++)
 #pragma unroll
@@ -331,7 +354,7 @@ template <int LOGN, int NT, int I, bool BASE0, class RED = RedAlg2, class L>
 __device__ __forceinline__ void inv_pass(const L &lay, int tid, const uint32_t *__restrict__ itw, int s_base, int b,
                                          Mod m)
 {
-    using PG = PassGeom<LOGN, NT, I>;
+    using PG = PassGeom<LOGN, NT, I, L::kAdditive>;
 #pragma unroll
     for (int r = 0; r < PG::GPT; r++) {
         const int base = PG::base(tid, r), blk = PG::blk(tid, r);
