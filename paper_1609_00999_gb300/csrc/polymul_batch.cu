@@ -216,6 +216,13 @@ __device__ __forceinline__ void col_tile(uint32_t *smem, const Prod &P, const Pr
     }
 }
 
+// Hint that the 128-byte line holding p will be read soon: fetched into L2,
+// no register written, nothing to wait for.
+__device__ __forceinline__ void prefetch_l2(const void *p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // Columns per job for the register column jobs: 2^14 elements per operand.
 constexpr int reg_cols(int k1) { return (1 << 14) >> k1 < (1 << kRowLog) ? (1 << 14) >> k1 : (1 << kRowLog); }
 
@@ -226,20 +233,38 @@ constexpr int reg_cols(int k1) { return (1 << 14) >> k1 < (1 << kRowLog) ? (1 <<
 // covers 32 consecutive words, and all of a thread's loads of a step are
 // independent, so they are in flight together.  The columns of a step share
 // their twiddles (levels 0 .. K1-1, block 0 of the transform), so they run
-// as the NARR arrays of one register group.
+// as the NARR arrays of one register group.  A warp's slots of a step are
+// NA x 2^K1 whole 128-byte lines; while a step loads, lane l asks L2 for
+// line l of the warp's next step (one prefetch per thread), so the next
+// step's loads find their lines in L2.
 template <int K1, bool INV>
 __device__ __forceinline__ void col_regs(const Prod &P, const PrimeInfo &pr, uint32_t tile)
 {
     constexpr int N1 = 1 << K1, G = 16 / N1, STEPS = reg_cols(K1) / kThreads / G;
     constexpr int NA = INV ? G : 2 * G;
     static_assert(STEPS >= 1 && reg_cols(K1) % (kThreads * G) == 0, "register column job geometry");
+    static_assert(NA * N1 <= 32, "one line per lane");
     const size_t n = size_t{1} << P.k;
     const Mod md{pr.p, pr.pp};
     const size_t c0 = static_cast<size_t>(tile) * reg_cols(K1) + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    auto prefetch_step = [&](int st) {
+        if (st >= STEPS || lane >= NA * N1) return;
+        const int arr = lane / N1, t = lane % N1;   // slot (array, row) of this lane's line
+        const size_t j = c0 - lane + static_cast<size_t>(st) * G * kThreads + (arr % G) * kThreads +
+                         (static_cast<size_t>(t) << kRowLog);
+        if constexpr (!INV) {
+            const bool opb = arr >= G;
+            if (j < (opb ? P.lb : P.la)) prefetch_l2((opb ? P.b : P.a) + j);
+        } else {
+            prefetch_l2(P.ws + j);
+        }
+    };
 #pragma unroll 1
     for (int st = 0; st < STEPS; st++) {
         const size_t cs = c0 + static_cast<size_t>(st) * G * kThreads;
         uint32_t x[NA][N1];
+        prefetch_step(st + 1);
         if constexpr (!INV) {
 #pragma unroll
             for (int a = 0; a < 2; a++) {
@@ -296,10 +321,14 @@ __device__ __forceinline__ void col_regs_itft(const Prod &P, const PrimeInfo &pr
     constexpr int N1 = 1 << K1, G = 16 / N1, STEPS = reg_cols(K1) / kThreads / G;
     const Mod md{pr.p, pr.pp};
     const size_t c0 = static_cast<size_t>(tile) * reg_cols(K1) + threadIdx.x;
+    const int lane = threadIdx.x & 31;
 #pragma unroll 1
     for (int st = 0; st < STEPS; st++) {
         const size_t cs = c0 + static_cast<size_t>(st) * G * kThreads;
         uint32_t x[G][N1];
+        if (st + 1 < STEPS && lane < G * L)          // line (g, t) of the warp's next step, as in col_regs
+            prefetch_l2(P.ws + (c0 - lane + static_cast<size_t>(st + 1) * G * kThreads) + (lane / L) * kThreads +
+                        (static_cast<size_t>(lane % L) << kRowLog));
 #pragma unroll
         for (int g = 0; g < G; g++)
 #pragma unroll
