@@ -322,13 +322,16 @@ __device__ __forceinline__ void col_regs_itft(const Prod &P, const PrimeInfo &pr
     const Mod md{pr.p, pr.pp};
     const size_t c0 = static_cast<size_t>(tile) * reg_cols(K1) + threadIdx.x;
     const int lane = threadIdx.x & 31;
+    auto prefetch_step = [&](int st) {               // line (g, t) of the warp's step st, as in col_regs
+        if (st >= STEPS || lane >= G * L) return;
+        prefetch_l2(P.ws + (c0 - lane + static_cast<size_t>(st) * G * kThreads) + (lane / L) * kThreads +
+                    (static_cast<size_t>(lane % L) << kRowLog));
+    };
 #pragma unroll 1
     for (int st = 0; st < STEPS; st++) {
         const size_t cs = c0 + static_cast<size_t>(st) * G * kThreads;
         uint32_t x[G][N1];
-        if (st + 1 < STEPS && lane < G * L)          // line (g, t) of the warp's next step, as in col_regs
-            prefetch_l2(P.ws + (c0 - lane + static_cast<size_t>(st + 1) * G * kThreads) + (lane / L) * kThreads +
-                        (static_cast<size_t>(lane % L) << kRowLog));
+        prefetch_step(st + 1);
 #pragma unroll
         for (int g = 0; g < G; g++)
 #pragma unroll
