@@ -37,6 +37,15 @@ __device__ __forceinline__ int brev(int k)
     else return static_cast<int>(__brev(static_cast<unsigned>(k)) >> (32 - LOGN));
 }
 
+// The same for a compile-time k.
+template <int LOGN>
+constexpr int brev_c(int k)
+{
+    int r = 0;
+    for (int b = 0; b < LOGN; b++) r |= ((k >> b) & 1) << (LOGN - 1 - b);
+    return r;
+}
+
 // Natural-order I/O of a transform held in the padded layout at bit-reversed
 // positions (word k of the natural order sits at brev(k)).  A warp that
 // walks 32 consecutive k hits brev(k) at addresses whose low bits repeat,
@@ -46,6 +55,9 @@ __device__ __forceinline__ int brev(int k)
 // for a fixed r the 32 lanes then differ in bits 5 .. 9 of brev(k) (bits
 // 4 .. 8 for N = 2^11), which the padding word per 32 maps onto 32 distinct
 // banks.  Each lane moves its S words of global memory as S / 4 uint4.
+// S m and r < S have disjoint bits, so brev(S m + r) = brev(S m) | brev(r),
+// and the padded layout adds over disjoint bits: word r of a lane-step is
+// the step's pointer plus the compile-time offset of brev(r).
 template <int LOGN, int NT>
 struct BrevIO {
     static constexpr int N = 1 << LOGN;
@@ -105,13 +117,14 @@ k_ntt_fwd(NttArgs A)
             for (int i = 0; i < IO::STEPS; i++) {
                 const int k0 = IO::S * (tid + NT * i);
                 uint4 *dst = reinterpret_cast<uint4 *>(g + k0);
+                const uint32_t *src = lay[0].at(brev<LOGN>(k0));
 #pragma unroll
                 for (int q = 0; q < IO::S / 4; q++) {
                     uint4 v;
-                    v.x = csub(lay[0][brev<LOGN>(k0 + 4 * q)], A.p);
-                    v.y = csub(lay[0][brev<LOGN>(k0 + 4 * q + 1)], A.p);
-                    v.z = csub(lay[0][brev<LOGN>(k0 + 4 * q + 2)], A.p);
-                    v.w = csub(lay[0][brev<LOGN>(k0 + 4 * q + 3)], A.p);
+                    v.x = csub(src[PadLayout::off(brev_c<LOGN>(4 * q))], A.p);
+                    v.y = csub(src[PadLayout::off(brev_c<LOGN>(4 * q + 1))], A.p);
+                    v.z = csub(src[PadLayout::off(brev_c<LOGN>(4 * q + 2))], A.p);
+                    v.w = csub(src[PadLayout::off(brev_c<LOGN>(4 * q + 3))], A.p);
                     dst[q] = v;
                 }
             }
@@ -150,13 +163,13 @@ k_ntt_inv(NttArgs A)
                                     : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
             for (int i = 0; i < IO::STEPS; i++) {
-                const int k0 = IO::S * (tid + NT * i);
+                uint32_t *dst = lay.at(brev<LOGN>(IO::S * (tid + NT * i)));
 #pragma unroll
                 for (int q = 0; q < IO::S / 4; q++) {
-                    lay[brev<LOGN>(k0 + 4 * q)] = v[i][q].x;
-                    lay[brev<LOGN>(k0 + 4 * q + 1)] = v[i][q].y;
-                    lay[brev<LOGN>(k0 + 4 * q + 2)] = v[i][q].z;
-                    lay[brev<LOGN>(k0 + 4 * q + 3)] = v[i][q].w;
+                    dst[PadLayout::off(brev_c<LOGN>(4 * q))] = v[i][q].x;
+                    dst[PadLayout::off(brev_c<LOGN>(4 * q + 1))] = v[i][q].y;
+                    dst[PadLayout::off(brev_c<LOGN>(4 * q + 2))] = v[i][q].z;
+                    dst[PadLayout::off(brev_c<LOGN>(4 * q + 3))] = v[i][q].w;
                 }
             }
             staged = true;
