@@ -334,9 +334,22 @@ k_row_ntt(RowNttArgs A, size_t prod0)
         }
         __syncthreads();
         fwd_passes<K2, NT, 1, false, 1, NP - 1>(lay, threadIdx.x, A.tw, A.k1, r, md);
-        for (int k = threadIdx.x; k < N2; k += NT) g[k] = csub(lay[0][k], A.p);
+        // word tid + NT i: tid < NT and NT i on disjoint bits, so its padded
+        // position is this thread's pointer plus a compile-time offset
+        const uint32_t *src = lay[0].at(threadIdx.x);
+#pragma unroll
+        for (int i = 0; i < N2 / NT; i++) g[threadIdx.x + i * NT] = csub(src[PadLayout::off(i * NT)], A.p);
     } else {
-        stage_in<N2, NT>(lay[0], g, threadIdx.x, true, [](int k) { return k; });
+        {
+            // every load of the thread in flight before its first store; the
+            // padded positions as in the forward's output loop
+            uint32_t v[N2 / NT];
+#pragma unroll
+            for (int i = 0; i < N2 / NT; i++) v[i] = g[threadIdx.x + i * NT];
+            uint32_t *dst = lay[0].at(threadIdx.x);
+#pragma unroll
+            for (int i = 0; i < N2 / NT; i++) dst[PadLayout::off(i * NT)] = v[i];
+        }
         __syncthreads();
         inv_passes<K2, NT, false, NP - 1, 1>(lay[0], threadIdx.x, A.tw, A.k1, r, md);
         // pass 0 straight to global memory
