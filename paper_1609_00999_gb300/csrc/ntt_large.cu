@@ -307,11 +307,14 @@ struct RowNttArgs {
     uint32_t p, pp;
 };
 
-template <int K2, bool INVERSE>
+// K1 >= 0: the column level count as a compile-time constant, so every
+// twiddle index of the row levels folds; K1 = -1 takes A.k1.
+template <int K2, int K1, bool INVERSE>
 __global__ void __launch_bounds__(nt_of<K2>(), K2 <= 13 ? 4 : 1)
 k_row_ntt(RowNttArgs A, size_t prod0)
 {
     constexpr int N2 = 1 << K2, NT = nt_of<K2>(), NP = SchedFor<K2, NT>::kPasses;
+    const int k1 = K1 >= 0 ? K1 : A.k1;
     extern __shared__ __align__(16) uint32_t smem[];
     const size_t prod = prod0 + blockIdx.y;
     const int r = blockIdx.x;
@@ -328,12 +331,12 @@ k_row_ntt(RowNttArgs A, size_t prod0)
             uint32_t x[1][P0::G];
 #pragma unroll
             for (int t = 0; t < P0::G; t++) x[0][t] = g[base + t * P0::HMIN];
-            ct_group<P0::E, 1, false>(x, A.tw, A.k1, (r << P0::S0) + P0::blk(threadIdx.x, q), md);
+            ct_group<P0::E, 1, false>(x, A.tw, k1, (r << P0::S0) + P0::blk(threadIdx.x, q), md);
 #pragma unroll
             for (int t = 0; t < P0::G; t++) elem(lay[0], base, t * P0::HMIN) = x[0][t];
         }
         __syncthreads();
-        fwd_passes<K2, NT, 1, false, 1, NP - 1>(lay, threadIdx.x, A.tw, A.k1, r, md);
+        fwd_passes<K2, NT, 1, false, 1, NP - 1>(lay, threadIdx.x, A.tw, k1, r, md);
         // word tid + NT i: tid < NT and NT i on disjoint bits, so its padded
         // position is this thread's pointer plus a compile-time offset
         const uint32_t *src = lay[0].at(threadIdx.x);
@@ -351,7 +354,7 @@ k_row_ntt(RowNttArgs A, size_t prod0)
             for (int i = 0; i < N2 / NT; i++) dst[PadLayout::off(i * NT)] = v[i];
         }
         __syncthreads();
-        inv_passes<K2, NT, false, NP - 1, 1>(lay[0], threadIdx.x, A.tw, A.k1, r, md);
+        inv_passes<K2, NT, false, NP - 1, 1>(lay[0], threadIdx.x, A.tw, k1, r, md);
         // pass 0 straight to global memory
 #pragma unroll
         for (int q = 0; q < P0::GPT; q++) {
@@ -359,7 +362,7 @@ k_row_ntt(RowNttArgs A, size_t prod0)
             uint32_t x[1][P0::G];
 #pragma unroll
             for (int t = 0; t < P0::G; t++) x[0][t] = elem(lay[0], base, t * P0::HMIN);
-            gs_group<P0::E, 1, false>(x, A.tw, A.k1, (r << P0::S0) + P0::blk(threadIdx.x, q), md);
+            gs_group<P0::E, 1, false>(x, A.tw, k1, (r << P0::S0) + P0::blk(threadIdx.x, q), md);
 #pragma unroll
             for (int t = 0; t < P0::G; t++) g[base + t * P0::HMIN] = x[0][t];
         }
@@ -453,15 +456,15 @@ int launch_row_polymul(const RowArgs &A, size_t count, cudaStream_t s, uint32_t 
     return MONT_OK;
 }
 
-template <int K2, bool INVERSE>
+template <int K2, int K1, bool INVERSE>
 int launch_row_ntt(const RowNttArgs &A, size_t count, cudaStream_t s)
 {
     const size_t smem = PadLayout::words(1 << K2) * sizeof(uint32_t);
-    if (ensure_smem(k_row_ntt<K2, INVERSE>, smem) != MONT_OK) return MONT_ECUDA;
+    if (ensure_smem(k_row_ntt<K2, K1, INVERSE>, smem) != MONT_OK) return MONT_ECUDA;
     const unsigned rows = static_cast<unsigned>(A.n >> K2);
     for (size_t first = 0; first < count; first += kMaxGridZ) {
         const unsigned y = static_cast<unsigned>(std::min<size_t>(kMaxGridZ, count - first));
-        k_row_ntt<K2, INVERSE><<<dim3(rows, y), nt_of<K2>(), smem, s>>>(A, first);
+        k_row_ntt<K2, K1, INVERSE><<<dim3(rows, y), nt_of<K2>(), smem, s>>>(A, first);
         if (cudaGetLastError() != cudaSuccess) return MONT_ECUDA;
     }
     return MONT_OK;
@@ -516,13 +519,22 @@ int dispatch_row_polymul(int k2, const RowArgs &A, size_t count, cudaStream_t s,
     }
 }
 
+// The (K2, K1) pairs split_k2 gives for N = 2^15 .. 2^24 have their own row
+// kernels; any other pair runs the kernel that reads K1 from its arguments.
 template <bool INVERSE>
 int dispatch_row_ntt(int k2, const RowNttArgs &A, size_t count, cudaStream_t s)
 {
+    switch (k2 * 16 + A.k1) {
+#define X(K2, K1) \
+    case K2 * 16 + K1: return launch_row_ntt<K2, K1, INVERSE>(A, count, s);
+        X(12, 3) X(12, 4) X(13, 4) X(14, 4) X(13, 6) X(13, 7) X(13, 8) X(13, 9) X(13, 10) X(14, 10)
+#undef X
+    default: break;
+    }
     switch (k2) {
-    case 12: return launch_row_ntt<12, INVERSE>(A, count, s);
-    case 13: return launch_row_ntt<13, INVERSE>(A, count, s);
-    case 14: return launch_row_ntt<14, INVERSE>(A, count, s);
+    case 12: return launch_row_ntt<12, -1, INVERSE>(A, count, s);
+    case 13: return launch_row_ntt<13, -1, INVERSE>(A, count, s);
+    case 14: return launch_row_ntt<14, -1, INVERSE>(A, count, s);
     default: return MONT_EUNSUPPORTED;
     }
 }

@@ -131,3 +131,31 @@ def test_truncated_single_products(m, la, lb):
         got = to_host(m.polymul_many(p, to_dev(a3), to_dev(b3))).reshape(3, la + lb - 1)
         for i in range(3):
             assert np.array_equal(got[i], oracle.polymul_ntt(p, a3[i], b3[i])), i
+
+
+@pytest.mark.parametrize("p,logn,rows", [(synth.P1, 19, 3), (synth.P2, 20, 2), (synth.P3, 21, 2)])
+def test_large_ntt_several_rows(m, p, logn, rows):
+    """Several rows of the direct column tiles and row kernels in one call
+    (the product index of the grid), each row against the oracle."""
+    n = 1 << logn
+    x = synth.residues(rows * n, p, 410, logn, rows).reshape(rows, n)
+    plan = m.ntt_plan_create(p, logn)
+    d = to_dev(x)
+    m.ntt_fwd(plan, d)
+    got = to_host(d).reshape(rows, n)
+    for i in range(rows):
+        assert np.array_equal(got[i], oracle.ntt(p, x[i])), i
+    m.ntt_inv(plan, d)
+    assert np.array_equal(to_host(d).reshape(rows, n), x)
+
+
+@pytest.mark.parametrize("p,la,lb", [(synth.P2, 200000, 100000), (synth.P1, 400000, 300000)])
+def test_large_polymul_many_split_sizes(m, p, la, lb):
+    """Two products of N = 2^19 and 2^20 (rows of 2^12) in one call, each
+    against the oracle."""
+    count = 2
+    a = synth.residues(count * la, p, 411, la, lb, 0).reshape(count, la)
+    b = synth.residues(count * lb, p, 411, la, lb, 1).reshape(count, lb)
+    got = to_host(m.polymul_many(p, to_dev(a), to_dev(b))).reshape(count, la + lb - 1)
+    for i in range(count):
+        assert np.array_equal(got[i], oracle.polymul_ntt(p, a[i], b[i])), i
